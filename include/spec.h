@@ -1,0 +1,166 @@
+/*
+ * spec.h -- C-ABI of the batched spectral-estimation library for sampled
+ * THz-TDS traces (zero-padded FFT, chirp-z transform, Zoom FFT), after
+ * García-Devesa, Báez-Chorro and Vidal, "Comparison of computing efficiency
+ * among FFT, CZT and Zoom FFT in THz-TDS", arXiv 2108.03948.
+ *
+ * Data layout shared by every transform
+ *   x   real float32 traces, row-major [batch][ld_x]; the first n samples of a
+ *       row are the trace x[n] = x(n T_s), T_s = 1/fs (Section 2.1, Eq. 1).
+ *   X   complex64 spectra, row-major [batch][ld_X], each element two floats
+ *       (re, im) interleaved; ld_X counts complex elements.
+ *   x and X may be device pointers (async on `stream`, no host sync) or host
+ *   pointers (pageable or pinned): host buffers are staged through
+ *   library-owned device memory and the call returns once X holds the result.
+ *   The caller owns x, X and the taps; the library owns only what sits in the
+ *   context (tables, caches, staging buffers).
+ *   `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *
+ * Errors
+ *   Every argument is validated before any launch; a bad one returns
+ *   SPEC_EINVAL and touches no memory.  Nothing aborts and nothing throws
+ *   across this boundary; spec_last_error() gives a one-line reason.
+ *   One context per host thread.
+ */
+#ifndef SPEC_H
+#define SPEC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPEC_API __attribute__((visibility("default")))
+#else
+#define SPEC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPEC_OK = 0,
+    SPEC_EINVAL = 1,        /* bad argument (checked before any launch)        */
+    SPEC_ENOMEM = 2,        /* device or host allocation failed                 */
+    SPEC_ECUDA = 3,         /* a CUDA runtime call failed                       */
+    SPEC_EUNSUPPORTED = 4,  /* valid arguments beyond this build's size limits  */
+    SPEC_ETIMEOUT = 5       /* a bounded device-side wait gave up               */
+} spec_status;
+
+/* How spec_czt evaluates the chirp-z transform.
+ *   SPEC_CZT_AUTO       the library picks (Bluestein unless a GEMM form is
+ *                       faster at the 1e-5 accuracy bar).
+ *   SPEC_CZT_BLUESTEIN  FP32 Bluestein: chirp, FFT convolution, chirp
+ *                       (Section 2.3, Eq. 13-15).                         */
+typedef enum {
+    SPEC_CZT_AUTO = 0,
+    SPEC_CZT_BLUESTEIN = 1
+} spec_czt_mode;
+
+typedef struct spec_ctx spec_ctx;
+
+/* Create a context bound to CUDA device `device`.  Allocates nothing large;
+ * tables are built on first use and cached.  Returns SPEC_EINVAL for a bad
+ * device index or a NULL out-pointer, SPEC_ECUDA if the device cannot be
+ * used.  On failure *ctx is set to NULL. */
+SPEC_API spec_status spec_ctx_create(spec_ctx** ctx, int device);
+
+/* Free every device buffer the context owns.  Synchronises the device.
+ * NULL is accepted. */
+SPEC_API void spec_ctx_destroy(spec_ctx* ctx);
+
+/* One-line reason for the last non-OK status returned on this context
+ * (empty string if none).  Valid until the next call on the context.
+ * A NULL context gives the reason of the last failed spec_ctx_create. */
+SPEC_API const char* spec_last_error(const spec_ctx* ctx);
+
+/* Wait for `stream` and report any deferred device-side error: SPEC_ECUDA
+ * for a CUDA error, SPEC_ETIMEOUT if a bounded device wait gave up. */
+SPEC_API spec_status spec_ctx_check(spec_ctx* ctx, void* stream);
+
+/*
+ * Zero-padded FFT of real traces (Section 2.1, Eq. 2 with the forward sign
+ * e^{-j 2 pi k n / N_FFT}; the zero-padding paragraph; resolution
+ * Delta f = fs/N_FFT, Eq. 3):
+ *
+ *     X[b][k] = sum_{n<N} x[b][n] e^{-j 2 pi k n / N_FFT},  k = 0 .. N_FFT/2
+ *
+ * The input is real, so the N_FFT/2 + 1 non-redundant bins are written
+ * (unnormalised); bin k is frequency k fs / N_FFT.
+ *   n      samples per trace, 1 <= n <= n_fft (no truncation)
+ *   n_fft  padded length, a power of two, 1 <= n_fft <= 2^24
+ *   fs     sampling frequency (> 0); defines the bin grid only
+ *   ld_x >= n, ld_X >= n_fft/2 + 1; x and X must not overlap.
+ */
+SPEC_API spec_status spec_fft(spec_ctx* ctx, const float* x, int64_t batch, int64_t n,
+                     int64_t ld_x, double fs, int64_t n_fft,
+                     float* X, int64_t ld_X, void* stream);
+
+/*
+ * Chirp-z transform on the unit circle (Section 2.3, Eq. 11 with Eq. 16-23,
+ * A_0 = W_0 = 1):
+ *
+ *     X[b][k] = sum_{n<N} x[b][n] A^{-n} W^{k n},  k = 0 .. M-1,
+ *     A = e^{j 2 pi f1/fs},  W = e^{-j 2 pi (f2 - f1)/(fs (M - 1))}
+ *
+ * i.e. the trace's spectrum at f_k = f1 + k (f2 - f1)/(M - 1): both band
+ * edges are bins (the (N_CZT - 1) of Eq. 18).  M = 1 gives the single bin
+ * at f1.  f2 < f1 is allowed (descending grid).  To get the paper's Eq. 24
+ * spacing (f2 - f1)/M pass f2' = f1 + (f2 - f1)(M - 1)/M.
+ * Unnormalised.  Bluestein form: X[k] = W^{k^2/2} [(x A^{-n} W^{n^2/2})
+ * (*) W^{-n^2/2}] (Eq. 13-15) over a power-of-two length L >= N + M - 1.
+ *   n >= 1, m >= 1, fs > 0, finite f1 and f2; ld_x >= n, ld_X >= m.
+ *   mode: see spec_czt_mode.
+ */
+SPEC_API spec_status spec_czt(spec_ctx* ctx, const float* x, int64_t batch, int64_t n,
+                     int64_t ld_x, double fs, double f1, double f2, int64_t m,
+                     int mode, float* X, int64_t ld_X, void* stream);
+
+/*
+ * Zoom FFT (Section 2.2, Eq. 6-10): the spectrum around the band centre
+ * f_N = (f1 + f2)/2 (Eq. 6) at the FFT's spacing fs/N_FFT:
+ *
+ *     y[n] = x[n] e^{-j 2 pi f_N n / fs}                  (Eq. 7, down-shift)
+ *     u[m] = sum_{k<L_h} h[k] y[m D - k],  y = 0 outside [0, N)   (Eq. 8-10)
+ *            m = 0 .. L_out - 1,  L_out = ceil((N + L_h - 1)/D)
+ *     U[j] = sum_m u[m] e^{-j 2 pi j m / K},  K = N_FFT / D       (Eq. 9)
+ *     X[b][i] = U[(i - K/2) mod K],  i = 0 .. K-1   (ascending frequency:
+ *               bin i is f_N + (i - K/2) fs / N_FFT)
+ *
+ *   taps   h[0 .. n_taps-1], float32, device or host pointer, used as given
+ *          (spec_design_lowpass makes the Hamming low-pass used by the
+ *          benchmarks)
+ *   d      decimation D >= 1, n_fft % d == 0, K = n_fft/d a power of two
+ *   L_out <= K is required (the kept samples must fit the K-point FFT).
+ *   ld_x >= n, ld_X >= K.
+ */
+SPEC_API spec_status spec_zoom(spec_ctx* ctx, const float* x, int64_t batch, int64_t n,
+                      int64_t ld_x, double fs, double f1, double f2, int64_t d,
+                      const float* taps, int64_t n_taps, int64_t n_fft,
+                      float* X, int64_t ld_X, void* stream);
+
+/* ---- host-only helpers (pure functions, no CUDA calls) ----------------- */
+
+/* Zeros to append to an N_FFT-sample record so that its bin spacing shrinks
+ * by `delta` (Section 2.1, Eq. 4-5: Delta = fs/N_FFT - fs/(N_FFT + x),
+ * x = fs N_FFT/(fs - Delta N_FFT) - N_FFT), rounded up to the smallest
+ * integer that reaches delta.  Returns -1 if fs <= 0, n_fft <= 0, delta < 0
+ * or delta >= fs/n_fft. */
+SPEC_API int64_t spec_zeros_for_delta(double fs, int64_t n_fft, double delta);
+
+/* CZT points giving the FFT's spacing over [f1, f2] (Section 2.3, Eq. 25:
+ * N_CZT = (f2 - f1)/fs N_FFT), rounded up; at least 1.  -1 for fs <= 0 or
+ * n_fft <= 0. */
+SPEC_API int64_t spec_m_for_resolution(double fs, double f1, double f2, int64_t n_fft);
+
+/* Low-pass FIR for the Zoom FFT decimator (Section 2.2, Eq. 8 realised as a
+ * finite filter): Hamming-windowed sinc with cutoff fs/(2D),
+ * h[k] = (0.54 - 0.46 cos(2 pi k/(L_h - 1))) sinc((k - (L_h - 1)/2)/D)/D,
+ * scaled so that sum h = D.  Writes n_taps floats to host memory `taps`.
+ * SPEC_EINVAL for n_taps < 1, d < 1 or taps == NULL. */
+SPEC_API spec_status spec_design_lowpass(float* taps, int64_t n_taps, int64_t d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPEC_H */

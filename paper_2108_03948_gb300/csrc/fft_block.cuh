@@ -1,0 +1,254 @@
+// fft_block.cuh -- device building blocks shared by the transform kernels.
+//
+// * complex helpers and in-register DFTs of size 2, 4, 8, 16;
+// * BlockFFT: a power-of-two complex FFT executed by a group of T threads,
+//   each holding E = LF/T elements in registers.  Before and after the
+//   transform thread t holds elements t + T*i (i < E) in natural order, so
+//   loads, pointwise products and stores need no shared-memory staging; only
+//   the Stockham passes in between exchange through shared memory.
+// * exact phases: a phase in cycles is kept as a 64-bit fixed-point fraction,
+//   so products such as (b/2) n^2 are reduced modulo one cycle exactly by
+//   integer wrap-around before any floating-point trig call.
+//
+// The FFT itself is the DFT of Section 2.1, Eq. 2 (forward sign e^{-j...});
+// the inverse (used by Bluestein's convolution, Eq. 15) flips the sign.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spec {
+
+// ---------------------------------------------------------------- complex --
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// multiply by e^{-j pi/2} (forward) or e^{+j pi/2} (inverse)
+template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// e^{-j 2 pi num/den} (forward) for an exact rational argument; sincospif
+// takes pi-multiples, so 2 num/den is passed (exact for den <= 2^24).
+template <bool INV> __device__ __forceinline__ float2 unit_rational(int num, int den) {
+    float s, c;
+    sincospif(2.0f * (float)num / (float)den, &s, &c);
+    return INV ? make_float2(c, s) : make_float2(c, -s);
+}
+
+// e^{sign j 2 pi ph/2^64}: `ph` is a phase in cycles as a 64-bit fixed-point
+// fraction.  The top bits go through sincospif; the remainder (below 2^-24
+// of a half-cycle) is applied to first order, so the result is accurate to
+// about 1e-8 absolute whatever the size of the original phase.
+__device__ __forceinline__ float2 unit_fixed(uint64_t ph, bool negative) {
+    const int64_t s = (int64_t)ph;                     // cycles in [-1/2, 1/2) * 2^64
+    const int32_t hi = (int32_t)(s >> 32);
+    const float hf = (float)hi;                        // rounded to 24 bits
+    // small remainder; unsigned arithmetic, because hf may round up to 2^31
+    const int64_t rem = (int64_t)((uint64_t)s - ((uint64_t)(int64_t)hf << 32));
+    const float xf = hf * 4.656612873077393e-10f;      // * 2^-31 (half-cycles)
+    const float xr = (float)rem * 1.0842021724855044e-19f * 3.14159265358979f;  // * 2^-63 * pi
+    float sn, cs;
+    sincospif(xf, &sn, &cs);
+    float re = fmaf(-xr, sn, cs);
+    float im = fmaf(xr, cs, sn);
+    return negative ? make_float2(re, -im) : make_float2(re, im);
+}
+
+// ------------------------------------------------------ in-register DFTs --
+template <bool INV> __device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+    float2 t = csub(a0, a1);
+    a0 = cadd(a0, a1);
+    a1 = t;
+}
+
+template <bool INV> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    float2 t2 = cadd(a1, a3), t3 = rot90<INV>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+constexpr float kS2 = 0.70710678118654752f;   // cos(pi/4)
+constexpr float kC8 = 0.92387953251128674f;   // cos(pi/8)
+constexpr float kS8 = 0.38268343236508978f;   // sin(pi/8)
+
+// multiply by w16^P = e^{-j 2 pi P/16} (forward) or its conjugate (inverse)
+template <int P, bool INV> __device__ __forceinline__ float2 tw16(float2 a) {
+    constexpr int Q = P & 15;
+    if constexpr (Q == 0) return a;
+    else if constexpr (Q == 4) return rot90<INV>(a);
+    else if constexpr (Q == 8) return make_float2(-a.x, -a.y);
+    else if constexpr (Q == 12) return rot90<!INV>(a);
+    else {
+        // cos / sin of 2 pi Q/16 for Q in {1,2,3,5,6,7,9,10,11,13,14,15}
+        constexpr float c = (Q == 1 || Q == 15) ? kC8 : (Q == 2 || Q == 14) ? kS2 : (Q == 3 || Q == 13) ? kS8
+                          : (Q == 5 || Q == 11) ? -kS8 : (Q == 6 || Q == 10) ? -kS2 : -kC8;
+        constexpr float s = (Q == 1 || Q == 7) ? kS8 : (Q == 2 || Q == 6) ? kS2 : (Q == 3 || Q == 5) ? kC8
+                          : (Q == 9 || Q == 15) ? -kS8 : (Q == 10 || Q == 14) ? -kS2 : -kC8;
+        // forward: e^{-j theta} = (c, -s); inverse: (c, s)
+        constexpr float wi = INV ? s : -s;
+        return make_float2(fmaf(a.x, c, -a.y * wi), fmaf(a.x, wi, a.y * c));
+    }
+}
+
+template <bool INV> __device__ __forceinline__ void dft8(float2* a) {
+    dft4<INV>(a[0], a[2], a[4], a[6]);
+    dft4<INV>(a[1], a[3], a[5], a[7]);
+    float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    float2 o0 = a[1], o1 = tw16<2, INV>(a[3]), o2 = tw16<4, INV>(a[5]), o3 = tw16<6, INV>(a[7]);
+    a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+    a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+    a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.
+template <bool INV> __device__ __forceinline__ void dft16(float2* a) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+    // slot 4 k1 + n2 now holds B[n2][k1]; twiddle by w16^{n2 k1}
+    a[5] = tw16<1, INV>(a[5]);  a[6] = tw16<2, INV>(a[6]);   a[7] = tw16<3, INV>(a[7]);
+    a[9] = tw16<2, INV>(a[9]);  a[10] = tw16<4, INV>(a[10]); a[11] = tw16<6, INV>(a[11]);
+    a[13] = tw16<3, INV>(a[13]); a[14] = tw16<6, INV>(a[14]); a[15] = tw16<9, INV>(a[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    // slot 4 k1 + k2 holds X[k1 + 4 k2]: transpose the 4x4 (register renaming)
+    float2 t;
+    t = a[1]; a[1] = a[4]; a[4] = t;
+    t = a[2]; a[2] = a[8]; a[8] = t;
+    t = a[3]; a[3] = a[12]; a[12] = t;
+    t = a[6]; a[6] = a[9]; a[9] = t;
+    t = a[7]; a[7] = a[13]; a[13] = t;
+    t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+template <int R, bool INV> __device__ __forceinline__ void dft(float2* a) {
+    if constexpr (R == 2) dft2<INV>(a[0], a[1]);
+    else if constexpr (R == 4) dft4<INV>(a[0], a[1], a[2], a[3]);
+    else if constexpr (R == 8) dft8<INV>(a);
+    else if constexpr (R == 16) dft16<INV>(a);
+}
+
+// w[r] = e^{-+j 2 pi k r/S}, r = 0 .. R-1.  Two sincospif calls (w, w^4)
+// and products of depth <= 3 keep the error within a few ulp.
+template <int R, bool INV> __device__ __forceinline__ void twiddle_powers(float2* w, int k, int S) {
+    w[0] = make_float2(1.f, 0.f);
+    if constexpr (R > 1) {
+        w[1] = unit_rational<INV>(k, S);
+        if constexpr (R >= 4) { w[2] = cmul(w[1], w[1]); w[3] = cmul(w[2], w[1]); }
+        if constexpr (R >= 8) {
+            w[4] = unit_rational<INV>(4 * k, S);
+            w[5] = cmul(w[4], w[1]); w[6] = cmul(w[4], w[2]); w[7] = cmul(w[4], w[3]);
+        }
+        if constexpr (R >= 16) {
+            w[8] = cmul(w[4], w[4]);
+#pragma unroll
+            for (int r = 9; r < 12; ++r) w[r] = cmul(w[8], w[r - 8]);
+            w[12] = cmul(w[8], w[4]);
+#pragma unroll
+            for (int r = 13; r < 16; ++r) w[r] = cmul(w[12], w[r - 12]);
+        }
+    }
+}
+
+// a[r] *= w^r, w = e^{-+j 2 pi k/S}, r = 1 .. R-1.
+template <int R, bool INV> __device__ __forceinline__ void apply_twiddles(float2* a, int k, int S) {
+    if constexpr (R > 1) {
+        float2 w[R];
+        twiddle_powers<R, INV>(w, k, S);
+#pragma unroll
+        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[r]);
+    }
+}
+
+// Padded shared-memory index: one spare slot per 16 keeps the stride-R writes
+// of the first Stockham pass free of bank conflicts.
+__host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+// ---------------------------------------------------------------- BlockFFT --
+// LF-point FFT by T = LF/E threads.  Radix plan: radix-16 passes, then one
+// pass of the remaining factor (2, 4 or 8).  `s` points at padded_len(LF)
+// float2 of shared memory owned by this FFT; `t` is the thread's index in
+// [0, T).  Every thread of the CTA must call run() (it contains
+// __syncthreads), including threads whose data are dummies.
+template <int LF> struct FFTShape {
+    static constexpr int E = LF < 16 ? LF : 16;
+    static constexpr int T = LF / E;
+    static constexpr int LOG = ilog2c(LF);
+    static constexpr int NP16 = LOG / 4;               // radix-16 passes
+    static constexpr int REM = 1 << (LOG % 4);         // trailing radix
+    static constexpr int NPASS = NP16 + (REM > 1 ? 1 : 0);
+    static constexpr int radix(int p) { return p < NP16 ? 16 : REM; }
+    static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
+};
+
+template <int LF, bool INV> struct BlockFFT {
+    using S = FFTShape<LF>;
+    static constexpr int E = S::E;
+    static constexpr int T = S::T;
+
+    template <int P>
+    static __device__ __forceinline__ void compute(float2 (&v)[E], int t) {
+        constexpr int R = S::radix(P);
+        constexpr int NS = S::ns(P);
+        constexpr int NB = E / R;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            float2 a[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[r] = v[b + r * NB];
+            if constexpr (NS > 1) {
+                const int j = t + T * b;
+                apply_twiddles<R, INV>(a, j & (NS - 1), NS * R);
+            }
+            dft<R, INV>(a);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b + r * NB] = a[r];
+        }
+    }
+
+    // Write the outputs of pass P to their Stockham positions, then read the
+    // thread's next inputs t + T i.
+    template <int P>
+    static __device__ __forceinline__ void exchange(float2 (&v)[E], float2* s, int t) {
+        constexpr int R = S::radix(P);
+        constexpr int NS = S::ns(P);
+        constexpr int NB = E / R;
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = t + T * b;
+            const int k = j & (NS - 1);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[pidx(base + r * NS)] = v[b + r * NB];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = s[pidx(t + T * i)];
+    }
+
+    template <int P>
+    static __device__ __forceinline__ void passes(float2 (&v)[E], float2* s, int t) {
+        if constexpr (P < S::NPASS) {
+            if constexpr (P > 0) exchange<P - 1>(v, s, t);
+            compute<P>(v, t);
+            passes<P + 1>(v, s, t);
+        }
+    }
+
+    static __device__ __forceinline__ void run(float2 (&v)[E], float2* s, int t) { passes<0>(v, s, t); }
+};
+
+}  // namespace spec

@@ -1,0 +1,168 @@
+// k_czt.cu -- chirp-z transform on the unit circle by Bluestein's method
+// (Section 2.3, Eq. 11-15).
+//
+// With z_k = e^{j 2 pi (a + b k)}, a = f1/fs, b = step/fs, and the identity
+// k n = (k^2 + n^2 - (k - n)^2)/2 (Eq. 12):
+//
+//   X[k] = post[k] * sum_n (x[n] pre[n]) v[k - n]                (Eq. 13-14)
+//   pre[n] = e^{-j 2 pi (a n + (b/2) n^2)},  post[k] = e^{-j 2 pi (b/2) k^2},
+//   v[m]  = e^{+j 2 pi (b/2) m^2},  m = -(N-1) .. M-1.
+//
+// The convolution is circular over a power-of-two L >= N + M - 1 with v
+// wrapped (negative m at L + m), evaluated as IFFT(FFT(x pre) * FFT(v))
+// (Eq. 15).  FFT(v)/L, pre and post depend only on (N, M, a, b): they are
+// built once in float64 from exact fixed-point phases and cached by the
+// caller, so each trace costs one FFT and one IFFT, both in shared memory,
+// with one HBM read of x and one write of X.
+#include "fft_block.cuh"
+#include "spec_internal.h"
+
+namespace spec {
+
+// e^{sign j 2 pi ph/2^64} evaluated in float64 (table generation only).
+__device__ __forceinline__ float2 unit_fixed_f64(uint64_t ph, bool negative) {
+    const double cyc = (double)(int64_t)ph * 5.421010862427522e-20;   // * 2^-64
+    double s, c;
+    sincospi(2.0 * cyc, &s, &c);
+    return make_float2((float)c, negative ? (float)-s : (float)s);
+}
+
+__global__ void k_czt_pre_post(float2* pre, int n, float2* post, int m, uint64_t A, uint64_t Bh) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t ii = (uint64_t)i;
+    if (i < n) pre[i] = unit_fixed_f64(A * ii + Bh * (ii * ii), true);
+    if (i < m) post[i] = unit_fixed_f64(Bh * (ii * ii), true);
+}
+
+// V = FFT_L(v)/L for the wrapped chirp kernel v; one CTA.
+template <int L>
+__global__ void __launch_bounds__(FFTShape<L>::T) k_czt_kernel_spectrum(float2* V, int n, int m, uint64_t Bh) {
+    using FFT = BlockFFT<L, false>;
+    constexpr int E = FFT::E, T = FFT::T;
+    extern __shared__ float2 smem[];
+    const int t = threadIdx.x;
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int idx = t + T * i;
+        int64_t mm;
+        bool nz = true;
+        if (idx < m) mm = idx;
+        else if (idx >= L - n + 1) mm = (int64_t)idx - L;
+        else { nz = false; mm = 0; }
+        const uint64_t m2 = (uint64_t)(mm * mm);
+        v[i] = nz ? unit_fixed_f64(Bh * m2, false) : make_float2(0.f, 0.f);
+    }
+    FFT::run(v, smem, t);
+    const float inv = 1.0f / (float)L;
+#pragma unroll
+    for (int i = 0; i < E; ++i) V[t + T * i] = cscale(v[i], inv);
+}
+
+struct BluesteinArgs {
+    const float* x;
+    int64_t batch;
+    int n;
+    int64_t ld_x;
+    int m;
+    const float2* pre;
+    const float2* V;
+    const float2* post;
+    float2* X;
+    int64_t ld_X;
+    int F;
+};
+
+template <int L>
+__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256) k_czt_bluestein(BluesteinArgs a) {
+    using Fw = BlockFFT<L, false>;
+    using Iv = BlockFFT<L, true>;
+    constexpr int E = Fw::E, T = Fw::T;
+    extern __shared__ float2 smem[];
+    const int f = threadIdx.x / T;
+    const int t = threadIdx.x - f * T;
+    const int64_t b = (int64_t)blockIdx.x * a.F + f;
+    const bool live = b < a.batch;
+    float2* s = smem + f * padded_len(L);
+    const float* xr = a.x + (live ? b : 0) * a.ld_x;
+
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int nn = t + T * i;
+        v[i] = (live && nn < a.n) ? cscale(__ldg(&a.pre[nn]), __ldg(xr + nn)) : make_float2(0.f, 0.f);
+    }
+    Fw::run(v, s, t);
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(&a.V[t + T * i]));
+    Iv::run(v, s, t);
+    float2* Xr = a.X + (live ? b : 0) * a.ld_X;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = t + T * i;
+        if (live && k < a.m) Xr[k] = cmul(v[i], __ldg(&a.post[k]));
+    }
+}
+
+using BsKernel = void (*)(BluesteinArgs);
+using VKernel = void (*)(float2*, int, int, uint64_t);
+
+template <int L> static void pick(int want, BsKernel* bk, VKernel* vk) {
+    if (want == L) { *bk = k_czt_bluestein<L>; *vk = k_czt_kernel_spectrum<L>; }
+}
+
+static bool kernels_for(int L, BsKernel* bk, VKernel* vk) {
+    *bk = nullptr; *vk = nullptr;
+    pick<16>(L, bk, vk); pick<32>(L, bk, vk); pick<64>(L, bk, vk); pick<128>(L, bk, vk);
+    pick<256>(L, bk, vk); pick<512>(L, bk, vk); pick<1024>(L, bk, vk); pick<2048>(L, bk, vk);
+    pick<4096>(L, bk, vk); pick<8192>(L, bk, vk); pick<16384>(L, bk, vk);
+    return *bk != nullptr;
+}
+
+int czt_length(int64_t n, int64_t m) { return (int)std::max<int64_t>(16, next_pow2(n + m - 1)); }
+
+bool czt_supported(int64_t n, int64_t m, std::string* why) {
+    if (n + m - 1 > 16384) {
+        *why = "CZT: N + M - 1 above 16384 needs the multi-pass Bluestein path";
+        return false;
+    }
+    return true;
+}
+
+cudaError_t czt_build_tables(const CztTables& t, cudaStream_t st) {
+    BsKernel bk;
+    VKernel vk;
+    if (!kernels_for(t.L, &bk, &vk)) return cudaErrorInvalidValue;
+    const int cnt = std::max(t.n, t.m);
+    k_czt_pre_post<<<(cnt + 255) / 256, 256, 0, st>>>(t.pre, t.n, t.post, t.m, t.A, t.Bh);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)padded_len(t.L) * sizeof(float2);
+    e = cudaFuncSetAttribute(vk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int T = t.L / 16;
+    vk<<<1, T, smem, st>>>(t.V, t.n, t.m, t.Bh);
+    return cudaGetLastError();
+}
+
+cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
+                       float2* X, int64_t ld_X, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    BsKernel bk;
+    VKernel vk;
+    if (!kernels_for(t.L, &bk, &vk)) return cudaErrorInvalidValue;
+    const int T = t.L / 16;
+    int F = std::max(1, 256 / T);
+    F = (int)std::min<int64_t>(F, batch);
+    const size_t smem = (size_t)F * padded_len(t.L) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    BluesteinArgs a;
+    a.x = x; a.batch = batch; a.n = t.n; a.ld_x = ld_x; a.m = t.m;
+    a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F;
+    const int64_t grid = (batch + F - 1) / F;
+    bk<<<(unsigned)grid, F * T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace spec

@@ -1,0 +1,222 @@
+// k_fft.cu -- zero-padded FFT of real traces (Section 2.1, Eq. 2-3 and the
+// zero-padding paragraph): X[k] = sum_{n<N} x[n] e^{-j 2 pi k n/N_FFT},
+// k = 0 .. N_FFT/2.
+//
+// Method (one launch, one HBM read of x and one write of X):
+//  1. pack pairs of real samples, z[m] = x[2m] + j x[2m+1], m < ceil(N/2),
+//     a complex sequence of H = N_FFT/2 points of which only LZ are nonzero;
+//  2. prune the padding: bin R q + r of the H-point FFT equals bin q of the
+//     LZ-point FFT of z[m] w_H^{r m} (R = H/LZ residues), so R dense LZ-point
+//     FFTs replace the sparse H-point one;
+//  3. unpack: X[k] = (Z[k] + conj Z[H-k])/2 - j/2 w^k (Z[k] - conj Z[H-k]),
+//     w = e^{-j 2 pi/N_FFT}, for the pair (k, H - k) at once.
+// Each CTA holds <= 8192 complex points; a trace that needs more is spread
+// over a thread-block cluster whose CTAs read each other's residues through
+// distributed shared memory in step 3.
+#include <cooperative_groups.h>
+
+#include "fft_block.cuh"
+#include "spec_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace spec {
+
+struct FftArgs {
+    const float* x;
+    int64_t batch;
+    int n;
+    int64_t ld_x;
+    int H, logR, Rc, C, F, Sr;
+    float2* X;
+    int64_t ld_X;
+};
+
+template <int LZ>
+__global__ void __launch_bounds__(512) k_fft_real_padded(FftArgs a) {
+    using FFT = BlockFFT<LZ, false>;
+    constexpr int E = FFT::E;
+    constexpr int T = FFT::T;
+    extern __shared__ float2 smem[];
+
+    const int per_trace = a.Rc * T;
+    const int tid = threadIdx.x;
+    const int f = tid / per_trace;
+    const int lt = tid - f * per_trace;          // thread index within the trace
+    const int rl = lt / T;
+    const int t = lt - rl * T;
+    const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
+    const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
+    const bool live = b < a.batch;
+    const int r = rank * a.Rc + rl;              // residue of this thread's FFT
+    const int H = a.H;
+    float2* s = smem + (f * a.Rc + rl) * a.Sr;
+
+    // 1-2. packed, pre-twiddled input: v[i] = z[m] w_H^{r m}, m = t + T i.
+    float2 v[E];
+    {
+        float2 wi[E];
+        twiddle_powers<E, false>(wi, r * T, H);   // (w_H^{r T})^i
+        const float2 wt = unit_rational<false>(r * t, H);
+        const float* xr = a.x + (live ? b : 0) * a.ld_x;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float re = 0.f, im = 0.f;
+            if (live && 2 * m < a.n) re = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < a.n) im = __ldg(xr + 2 * m + 1);
+            v[i] = cmul(make_float2(re, im), cmul(wt, wi[i]));
+        }
+    }
+    FFT::run(v, s, t);
+
+    // v[i] = Z[R q + r], q = t + T i.  Stage Z for the pairing step.
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E; ++i) s[pidx(t + T * i)] = v[i];
+    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
+
+    // 3. unpack pairs (k, H - k), k = 0 .. H/2, split over the cluster.
+    const int R = 1 << a.logR;
+    const int pairs = H / 2 + 1;
+    const int per_cta = (pairs + a.C - 1) / a.C;
+    const int k0 = rank * per_cta;
+    const int k1 = min(pairs, k0 + per_cta);
+    float2* Xr = a.X + (live ? b : 0) * a.ld_X;
+    const int N_FFT = 2 * H;
+    for (int k = k0 + lt; k < k1 && live; k += per_trace) {
+        const int kb = (H - k) & (H - 1);
+        float2 A, B;
+        {
+            const int ra = k & (R - 1), rb = kb & (R - 1);
+            const int qa = k >> a.logR, qb = kb >> a.logR;
+            const float2* sa = smem + (f * a.Rc + (ra % a.Rc)) * a.Sr;
+            const float2* sb = smem + (f * a.Rc + (rb % a.Rc)) * a.Sr;
+            if (a.C > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                sa = cl.map_shared_rank(sa, ra / a.Rc);
+                sb = cl.map_shared_rank(sb, rb / a.Rc);
+            }
+            A = sa[pidx(qa)];
+            B = sb[pidx(qb)];
+        }
+        const float2 w = unit_rational<false>(k, N_FFT);    // e^{-j 2 pi k/N_FFT}
+        // X[k] = (A + conj B)/2 - j/2 w (A - conj B)
+        const float2 sp = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+        const float2 dm = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y + B.y));
+        const float2 wd = cmul(w, dm);
+        Xr[k] = make_float2(sp.x + wd.y, sp.y - wd.x);
+        if (H - k != k) {
+            // X[H-k] = (B + conj A)/2 - j/2 w' (B - conj A), w' = -conj(w)
+            const float2 sp2 = make_float2(sp.x, -sp.y);
+            const float2 dm2 = make_float2(-dm.x, dm.y);
+            const float2 wd2 = cmul(make_float2(-w.x, w.y), dm2);
+            Xr[H - k] = make_float2(sp2.x + wd2.y, sp2.y - wd2.x);
+        }
+    }
+    if (a.C > 1) cg::this_cluster().sync();   // keep shared memory alive for readers
+}
+
+// n_fft == 1: the single bin is x[0].
+__global__ void k_fft_len1(const float* x, int64_t batch, int64_t ld_x, float2* X, int64_t ld_X) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < batch) X[b * ld_X] = make_float2(x[b * ld_x], 0.f);
+}
+
+using FftKernel = void (*)(FftArgs);
+
+static FftKernel fft_kernel_for(int LZ) {
+    switch (LZ) {
+        case 1: return k_fft_real_padded<1>;
+        case 2: return k_fft_real_padded<2>;
+        case 4: return k_fft_real_padded<4>;
+        case 8: return k_fft_real_padded<8>;
+        case 16: return k_fft_real_padded<16>;
+        case 32: return k_fft_real_padded<32>;
+        case 64: return k_fft_real_padded<64>;
+        case 128: return k_fft_real_padded<128>;
+        case 256: return k_fft_real_padded<256>;
+        case 512: return k_fft_real_padded<512>;
+        case 1024: return k_fft_real_padded<1024>;
+        case 2048: return k_fft_real_padded<2048>;
+        case 4096: return k_fft_real_padded<4096>;
+        case 8192: return k_fft_real_padded<8192>;
+        default: return nullptr;
+    }
+}
+
+bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why) {
+    *p = FftPlan();
+    if (n_fft == 1) return true;
+    const int64_t H = n_fft / 2;
+    int64_t LZ = next_pow2((n + 1) / 2);
+    LZ = std::max<int64_t>(LZ, std::min<int64_t>(16, H));
+    LZ = std::min<int64_t>(LZ, H);
+    if (LZ > kTile) {
+        *why = "padded FFT: more than 16384 samples per trace needs the multi-pass path";
+        return false;
+    }
+    const int64_t R = H / LZ;
+    const int64_t C = std::max<int64_t>(1, H / kTile);
+    if (C > 8) {
+        *why = "padded FFT: n_fft above 131072 needs the multi-pass path";
+        return false;
+    }
+    const int E = LZ < 16 ? (int)LZ : 16;
+    const int T = (int)LZ / E;
+    p->H = (int)H;
+    p->LZ = (int)LZ;
+    p->R = (int)R;
+    p->C = (int)C;
+    p->Rc = (int)(R / C);
+    const int per_trace = p->Rc * T;
+    p->F = 1;
+    if (C == 1) {
+        int64_t F = std::max<int64_t>(1, 256 / per_trace);
+        F = std::min<int64_t>(F, std::max<int64_t>(1, batch));
+        p->F = (int)F;
+    }
+    // residue stride: spread the residues of one k-run over distinct banks
+    const int base = padded_len((int)LZ);
+    const int target = R >= 16 ? 1 : (int)((16 / R) & 15);
+    p->Sr = base + (((target - base) % 16) + 16) % 16;
+    p->threads = p->F * per_trace;
+    p->smem = (size_t)p->F * p->Rc * p->Sr * sizeof(float2);
+    return true;
+}
+
+cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
+                       float2* X, int64_t ld_X, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    if (p.H == 0) {   // n_fft == 1
+        k_fft_len1<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(x, batch, ld_x, X, ld_X);
+        return cudaGetLastError();
+    }
+    FftKernel k = fft_kernel_for(p.LZ);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    FftArgs a;
+    a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
+    a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = p.F; a.Sr = p.Sr;
+    a.X = X; a.ld_X = ld_X;
+    const int64_t groups = (batch + p.F - 1) / p.F;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(groups * p.C));
+    cfg.blockDim = dim3(p.threads);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    if (p.C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = p.C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
+}  // namespace spec

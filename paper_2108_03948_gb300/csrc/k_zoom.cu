@@ -1,0 +1,161 @@
+// k_zoom.cu -- Zoom FFT (Section 2.2, Eq. 6-10): mix the band centre f_N to
+// DC, low-pass FIR, keep every D-th sample, K-point FFT, ascending order.
+//
+// One CTA per trace, one HBM read of x and one write of the K bins.  The
+// mix is folded into the taps, which is the same sum regrouped:
+//
+//   u[m] = sum_k h[k] x[mD-k] e^{-j w (mD-k)}
+//        = e^{-j w mD} sum_k (h[k] e^{+j w k}) x[mD-k],   w = 2 pi f_N/fs,
+//
+// so the FIR runs on the real samples with complex taps g[k] and one
+// rotation per kept output.  Only the L_out = ceil((N + L_h - 1)/D) outputs
+// that are kept are computed.  The trace sits in shared memory split by
+// phase (x[iD + p] at row p, column i) so that the lanes of a warp, which
+// compute consecutive outputs m, read consecutive words for every tap.
+// Both phases (w k and w mD) are exact 64-bit fixed-point products.
+#include "fft_block.cuh"
+#include "spec_internal.h"
+
+namespace spec {
+
+struct ZoomArgs {
+    const float* x;
+    int64_t batch;
+    int n;
+    int64_t ld_x;
+    const float* taps;
+    int n_taps, d, lout, xlen, rs;
+    uint64_t Cn;
+    float2* X;
+    int64_t ld_X;
+};
+
+template <int K>
+__global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
+    using FFT = BlockFFT<K, false>;
+    constexpr int E = FFT::E, T = FFT::T;
+    extern __shared__ float4 smem4[];
+    const int t = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int J = a.n_taps - 1;
+    const int D = a.d;
+
+    // shared layout: taps {g.re, g.im, offset} | polyphase x | FFT exchange
+    float4* tap = smem4;
+    float* xs = reinterpret_cast<float*>(smem4 + a.n_taps);
+    float2* s = reinterpret_cast<float2*>(smem4 + a.n_taps) + (D * a.rs + 1) / 2;
+
+    // complex taps g[k] = h[k] e^{+j 2 pi c k} and their polyphase offsets
+    for (int k = t; k < a.n_taps; k += T) {
+        const float h = __ldg(a.taps + k);
+        const float2 e = unit_fixed(a.Cn * (uint64_t)k, false);
+        const int q = J - k;
+        const int off = (q % D) * a.rs + q / D;
+        tap[k] = make_float4(h * e.x, h * e.y, __int_as_float(off), 0.f);
+    }
+    // extended trace xe[j] = x[j - J] (zero outside [0, N)), by phase
+    const float* xr = a.x + b * a.ld_x;
+    for (int j = t; j < a.xlen; j += T) {
+        const int src = j - J;
+        const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
+        xs[(j % D) * a.rs + j / D] = xv;
+    }
+    __syncthreads();
+
+    // FIR + decimate: thread t owns outputs m = t + T i, the FFT's input layout
+    float2 v[E];
+    const int imax = (a.lout + T - 1) / T;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        v[i] = make_float2(0.f, 0.f);
+        if (i < imax) {
+            const int m = t + T * i;
+            if (m < a.lout) {
+                float re = 0.f, im = 0.f;
+                const float* xm = xs + m;
+                for (int k = 0; k < a.n_taps; ++k) {
+                    const float4 g = tap[k];
+                    const float xv = xm[__float_as_int(g.z)];
+                    re = fmaf(g.x, xv, re);
+                    im = fmaf(g.y, xv, im);
+                }
+                const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
+                v[i] = cmul(make_float2(re, im), rot);
+            }
+        }
+    }
+    FFT::run(v, s, t);
+    float2* Xr = a.X + b * a.ld_X;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int j = t + T * i;
+        Xr[(j + K / 2) & (K - 1)] = v[i];
+    }
+}
+
+using ZoomKernel = void (*)(ZoomArgs);
+
+static ZoomKernel zoom_kernel_for(int K) {
+    switch (K) {
+        case 1: return k_zoom<1>;
+        case 2: return k_zoom<2>;
+        case 4: return k_zoom<4>;
+        case 8: return k_zoom<8>;
+        case 16: return k_zoom<16>;
+        case 32: return k_zoom<32>;
+        case 64: return k_zoom<64>;
+        case 128: return k_zoom<128>;
+        case 256: return k_zoom<256>;
+        case 512: return k_zoom<512>;
+        case 1024: return k_zoom<1024>;
+        case 2048: return k_zoom<2048>;
+        case 4096: return k_zoom<4096>;
+        case 8192: return k_zoom<8192>;
+        case 16384: return k_zoom<16384>;
+        default: return nullptr;
+    }
+}
+
+bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
+               double f2, ZoomPlan* p, std::string* why) {
+    *p = ZoomPlan();
+    const int64_t K = n_fft / d;
+    const int64_t lout = (n + n_taps - 1 + d - 1) / d;
+    if (K > 16384) {
+        *why = "zoom: N_FFT/D above 16384 needs the multi-pass path";
+        return false;
+    }
+    const int64_t xlen = (lout - 1) * d + n_taps;
+    int64_t rs = (xlen + d - 1) / d + 1;
+    if ((rs & 1) == 0) ++rs;
+    const size_t smem = (size_t)n_taps * 16 + (size_t)((d * rs + 1) / 2) * 8 +
+                        (size_t)padded_len((int)K) * 8;
+    if (smem > 200 * 1024) {
+        *why = "zoom: trace plus taps exceed one CTA's shared memory; needs the multi-pass path";
+        return false;
+    }
+    p->n = (int)n; p->d = (int)d; p->n_taps = (int)n_taps; p->K = (int)K; p->lout = (int)lout;
+    p->xlen = (int)xlen; p->rs = (int)rs;
+    p->Cn = cycles_to_fixed(0.5 * (f1 + f2) / fs);
+    const int E = K < 16 ? (int)K : 16;
+    p->threads = (int)(K / E);
+    p->smem = smem;
+    return true;
+}
+
+cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
+                        const float* taps, float2* X, int64_t ld_X, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    ZoomKernel k = zoom_kernel_for(p.K);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    ZoomArgs a;
+    a.x = x; a.batch = batch; a.n = p.n; a.ld_x = ld_x; a.taps = taps;
+    a.n_taps = p.n_taps; a.d = p.d; a.lout = p.lout; a.xlen = p.xlen; a.rs = p.rs; a.Cn = p.Cn;
+    a.X = X; a.ld_X = ld_X;
+    k<<<(unsigned)batch, p.threads, p.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace spec

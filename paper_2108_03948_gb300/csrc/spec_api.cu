@@ -1,0 +1,390 @@
+// spec_api.cu -- the C-ABI declared in include/spec.h: context, argument
+// validation (before any launch), host-buffer staging, the Bluestein table
+// cache, and dispatch to the kernels.  No exception crosses the boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "spec.h"
+#include "spec_internal.h"
+
+namespace spec {
+
+uint64_t cycles_to_fixed(double cycles) {
+    double fr = cycles - std::floor(cycles);           // [0, 1)
+    double v = std::ldexp(fr, 64);
+    if (!(v < 18446744073709551616.0)) v = 0.0;        // fr rounded up to 1
+    return (uint64_t)v;
+}
+
+}  // namespace spec
+
+using namespace spec;
+
+struct CztEntry {
+    CztTables t;
+    void* mem = nullptr;
+    cudaEvent_t ready = nullptr;
+    uint64_t last_use = 0;
+};
+
+struct spec_ctx {
+    int device = 0;
+    std::string err;
+    std::vector<CztEntry> czt;
+    uint64_t tick = 0;
+    void* stage[3] = {nullptr, nullptr, nullptr};   // x, X, taps
+    size_t stage_bytes[3] = {0, 0, 0};
+};
+
+static std::string g_create_err;
+static const size_t kCztCacheMax = 64;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+spec_status fail(spec_ctx* c, spec_status s, const std::string& why) {
+    c->err = why;
+    return s;
+}
+
+spec_status cuda_fail(spec_ctx* c, cudaError_t e, const char* what) {
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SPEC_ENOMEM : SPEC_ECUDA;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+spec_status ensure_stage(spec_ctx* c, int slot, size_t bytes) {
+    if (c->stage_bytes[slot] >= bytes) return SPEC_OK;
+    if (c->stage[slot]) cudaFree(c->stage[slot]);
+    c->stage[slot] = nullptr;
+    c->stage_bytes[slot] = 0;
+    cudaError_t e = cudaMalloc(&c->stage[slot], bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "staging buffer");
+    c->stage_bytes[slot] = bytes;
+    return SPEC_OK;
+}
+
+// Where x (input rows) and X (output rows) live; host buffers get device
+// staging and a synchronous copy-back.
+struct Io {
+    const float* x = nullptr;
+    float2* X = nullptr;
+    bool x_host = false, X_host = false;
+};
+
+spec_status stage_in(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x,
+                     cudaStream_t st, Io* io) {
+    io->x_host = !is_device_ptr(x);
+    if (!io->x_host) {
+        io->x = x;
+        return SPEC_OK;
+    }
+    const size_t bytes = (size_t)((batch - 1) * ld_x + n) * sizeof(float);
+    spec_status s = ensure_stage(c, 0, bytes);
+    if (s != SPEC_OK) return s;
+    cudaError_t e = cudaMemcpy2DAsync(c->stage[0], ld_x * sizeof(float), x, ld_x * sizeof(float),
+                                      n * sizeof(float), batch, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy of x");
+    io->x = (const float*)c->stage[0];
+    return SPEC_OK;
+}
+
+spec_status stage_out_alloc(spec_ctx* c, float* X, int64_t batch, int64_t bins, int64_t ld_X, Io* io) {
+    io->X_host = !is_device_ptr(X);
+    if (!io->X_host) {
+        io->X = reinterpret_cast<float2*>(X);
+        return SPEC_OK;
+    }
+    const size_t bytes = (size_t)((batch - 1) * ld_X + bins) * sizeof(float2);
+    spec_status s = ensure_stage(c, 1, bytes);
+    if (s != SPEC_OK) return s;
+    io->X = (float2*)c->stage[1];
+    return SPEC_OK;
+}
+
+spec_status stage_out_finish(spec_ctx* c, float* X, int64_t batch, int64_t bins, int64_t ld_X,
+                             cudaStream_t st, const Io& io) {
+    if (!io.X_host && !io.x_host) return SPEC_OK;
+    if (io.X_host) {
+        cudaError_t e = cudaMemcpy2DAsync(X, ld_X * sizeof(float2), io.X, ld_X * sizeof(float2),
+                                          bins * sizeof(float2), batch, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy of X");
+    }
+    // host buffers: the caller may reuse them as soon as the call returns
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "transform");
+    return SPEC_OK;
+}
+
+spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x,
+                         double fs, const float* X, int64_t bins, int64_t ld_X) {
+    if (!x || !X) return fail(c, SPEC_EINVAL, "x and X must not be NULL");
+    if (batch < 0) return fail(c, SPEC_EINVAL, "batch must be >= 0");
+    if (n < 1 || n > (int64_t(1) << 24)) return fail(c, SPEC_EINVAL, "n must be in [1, 2^24]");
+    if (ld_x < n) return fail(c, SPEC_EINVAL, "ld_x must be >= n");
+    if (ld_X < bins) return fail(c, SPEC_EINVAL, "ld_X must be >= the number of output bins");
+    if (!(fs > 0.0) || !is_finite(fs)) return fail(c, SPEC_EINVAL, "fs must be finite and > 0");
+    if (batch > 0) {
+        const size_t bx = (size_t)((batch - 1) * ld_x + n) * sizeof(float);
+        const size_t bX = (size_t)((batch - 1) * ld_X + bins) * sizeof(float2);
+        if (overlaps(x, bx, X, bX)) return fail(c, SPEC_EINVAL, "x and X overlap");
+    }
+    return SPEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spec_status spec_ctx_create(spec_ctx** ctx, int device) {
+    if (!ctx) {
+        g_create_err = "ctx out-pointer is NULL";
+        return SPEC_EINVAL;
+    }
+    *ctx = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return SPEC_ECUDA;
+    }
+    if (device < 0 || device >= count) {
+        g_create_err = "device index out of range";
+        return SPEC_EINVAL;
+    }
+    DeviceGuard g(device);
+    e = cudaFree(nullptr);   // create the primary context now
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("cannot use device: ") + cudaGetErrorString(e);
+        return SPEC_ECUDA;
+    }
+    spec_ctx* c = new (std::nothrow) spec_ctx();
+    if (!c) {
+        g_create_err = "out of host memory";
+        return SPEC_ENOMEM;
+    }
+    c->device = device;
+    *ctx = c;
+    return SPEC_OK;
+}
+
+void spec_ctx_destroy(spec_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        cudaDeviceSynchronize();
+        for (auto& en : c->czt) {
+            if (en.mem) cudaFree(en.mem);
+            if (en.ready) cudaEventDestroy(en.ready);
+        }
+        for (int i = 0; i < 3; ++i)
+            if (c->stage[i]) cudaFree(c->stage[i]);
+        cudaGetLastError();
+    }
+    delete c;
+}
+
+const char* spec_last_error(const spec_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+spec_status spec_ctx_check(spec_ctx* c, void* stream) {
+    if (!c) return SPEC_EINVAL;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    c->err.clear();
+    return SPEC_OK;
+}
+
+spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
+                     int64_t n_fft, float* X, int64_t ld_X, void* stream) {
+    if (!c) return SPEC_EINVAL;
+    if (n_fft < 1 || n_fft > (int64_t(1) << 24) || !is_pow2(n_fft))
+        return fail(c, SPEC_EINVAL, "n_fft must be a power of two in [1, 2^24]");
+    const int64_t bins = n_fft / 2 + 1;
+    spec_status s = check_common(c, x, batch, n, ld_x, fs, X, bins, ld_X);
+    if (s != SPEC_OK) return s;
+    if (n_fft < n) return fail(c, SPEC_EINVAL, "n_fft must be >= n (padding never truncates)");
+    FftPlan p;
+    std::string why;
+    if (!fft_plan(batch, n, n_fft, &p, &why)) return fail(c, SPEC_EUNSUPPORTED, why);
+    if (batch == 0) return SPEC_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Io io;
+    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
+    if ((s = stage_out_alloc(c, X, batch, bins, ld_X, &io)) != SPEC_OK) return s;
+    cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, io.X, ld_X, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
+    return stage_out_finish(c, X, batch, bins, ld_X, st, io);
+}
+
+spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
+                     double f1, double f2, int64_t m, int mode, float* X, int64_t ld_X, void* stream) {
+    if (!c) return SPEC_EINVAL;
+    if (m < 1 || m > (int64_t(1) << 24)) return fail(c, SPEC_EINVAL, "m must be in [1, 2^24]");
+    spec_status s = check_common(c, x, batch, n, ld_x, fs, X, m, ld_X);
+    if (s != SPEC_OK) return s;
+    if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
+    if (mode != SPEC_CZT_AUTO && mode != SPEC_CZT_BLUESTEIN) return fail(c, SPEC_EINVAL, "unknown CZT mode");
+    std::string why;
+    if (!czt_supported(n, m, &why)) return fail(c, SPEC_EUNSUPPORTED, why);
+    if (batch == 0) return SPEC_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // Bluestein tables for (N, M, f1/fs, step/fs), cached
+    const double step = m > 1 ? (f2 - f1) / (double)(m - 1) : 0.0;
+    const uint64_t A = cycles_to_fixed(f1 / fs);
+    const uint64_t Bh = cycles_to_fixed(0.5 * (step / fs));
+    const int L = czt_length(n, m);
+    CztEntry* en = nullptr;
+    for (auto& it : c->czt)
+        if (it.t.n == n && it.t.m == m && it.t.L == L && it.t.A == A && it.t.Bh == Bh) en = &it;
+    if (!en) {
+        if (c->czt.size() >= kCztCacheMax) {
+            auto lru = std::min_element(c->czt.begin(), c->czt.end(),
+                                        [](const CztEntry& a, const CztEntry& b) { return a.last_use < b.last_use; });
+            cudaDeviceSynchronize();
+            cudaFree(lru->mem);
+            cudaEventDestroy(lru->ready);
+            c->czt.erase(lru);
+        }
+        CztEntry ne;
+        ne.t.n = (int)n; ne.t.m = (int)m; ne.t.L = L; ne.t.A = A; ne.t.Bh = Bh;
+        const size_t elems = (size_t)n + (size_t)L + (size_t)m;
+        cudaError_t e = cudaMalloc(&ne.mem, elems * sizeof(float2));
+        if (e != cudaSuccess) return cuda_fail(c, e, "CZT tables");
+        ne.t.pre = (float2*)ne.mem;
+        ne.t.V = ne.t.pre + n;
+        ne.t.post = ne.t.V + L;
+        e = cudaEventCreateWithFlags(&ne.ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) { cudaFree(ne.mem); return cuda_fail(c, e, "event"); }
+        e = czt_build_tables(ne.t, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
+        if (e != cudaSuccess) {
+            cudaFree(ne.mem);
+            cudaEventDestroy(ne.ready);
+            return cuda_fail(c, e, "CZT table build");
+        }
+        c->czt.push_back(ne);
+        en = &c->czt.back();
+    } else {
+        cudaError_t e = cudaStreamWaitEvent(st, en->ready, 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "table wait");
+    }
+    en->last_use = ++c->tick;
+
+    Io io;
+    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
+    if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
+    cudaError_t e = czt_launch(en->t, io.x, batch, ld_x, io.X, ld_X, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
+    return stage_out_finish(c, X, batch, m, ld_X, st, io);
+}
+
+spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
+                      double f1, double f2, int64_t d, const float* taps, int64_t n_taps, int64_t n_fft,
+                      float* X, int64_t ld_X, void* stream) {
+    if (!c) return SPEC_EINVAL;
+    if (d < 1) return fail(c, SPEC_EINVAL, "d must be >= 1");
+    if (n_fft < 1 || n_fft % d != 0 || !is_pow2(n_fft / d) || n_fft / d > (int64_t(1) << 24))
+        return fail(c, SPEC_EINVAL, "n_fft must be a multiple of d with n_fft/d a power of two");
+    const int64_t K = n_fft / d;
+    spec_status s = check_common(c, x, batch, n, ld_x, fs, X, K, ld_X);
+    if (s != SPEC_OK) return s;
+    if (!taps) return fail(c, SPEC_EINVAL, "taps must not be NULL");
+    if (n_taps < 1 || n_taps > 65536) return fail(c, SPEC_EINVAL, "n_taps must be in [1, 65536]");
+    if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
+    if ((n + n_taps - 1 + d - 1) / d > K)
+        return fail(c, SPEC_EINVAL, "ceil((n + n_taps - 1)/d) must not exceed n_fft/d");
+    ZoomPlan p;
+    std::string why;
+    if (!zoom_plan(n, d, n_taps, n_fft, fs, f1, f2, &p, &why)) return fail(c, SPEC_EUNSUPPORTED, why);
+    if (batch == 0) return SPEC_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float* taps_d = taps;
+    if (!is_device_ptr(taps)) {
+        if ((s = ensure_stage(c, 2, (size_t)n_taps * sizeof(float))) != SPEC_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(c->stage[2], taps, n_taps * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy of taps");
+        taps_d = (const float*)c->stage[2];
+    }
+    Io io;
+    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
+    if ((s = stage_out_alloc(c, X, batch, K, ld_X, &io)) != SPEC_OK) return s;
+    cudaError_t e = zoom_launch(p, io.x, batch, ld_x, taps_d, io.X, ld_X, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
+    return stage_out_finish(c, X, batch, K, ld_X, st, io);
+}
+
+// ---- host helpers ----------------------------------------------------------
+
+int64_t spec_zeros_for_delta(double fs, int64_t n_fft, double delta) {
+    if (!(fs > 0.0) || n_fft <= 0 || !(delta >= 0.0) || !(delta * (double)n_fft < fs)) return -1;
+    const double N = (double)n_fft;
+    const double xr = fs * N / (fs - delta * N) - N;   // Eq. 5
+    int64_t x = (int64_t)std::ceil(xr - 1e-9 * std::max(1.0, std::fabs(xr)));
+    if (x < 0) x = 0;
+    while (fs / N - fs / (N + (double)x) < delta * (1.0 - 1e-12)) ++x;
+    return x;
+}
+
+int64_t spec_m_for_resolution(double fs, double f1, double f2, int64_t n_fft) {
+    if (!(fs > 0.0) || n_fft <= 0) return -1;
+    const double v = std::fabs(f2 - f1) / fs * (double)n_fft;   // Eq. 25
+    int64_t m = (int64_t)std::ceil(v - 1e-9 * std::max(1.0, v));
+    return m < 1 ? 1 : m;
+}
+
+spec_status spec_design_lowpass(float* taps, int64_t n_taps, int64_t d) {
+    if (!taps || n_taps < 1 || d < 1) return SPEC_EINVAL;
+    std::vector<double> h((size_t)n_taps);
+    const double pi = 3.14159265358979323846;
+    const double mid = 0.5 * (double)(n_taps - 1);
+    double sum = 0.0;
+    for (int64_t k = 0; k < n_taps; ++k) {
+        const double w = n_taps == 1 ? 1.0 : 0.54 - 0.46 * std::cos(2.0 * pi * (double)k / (double)(n_taps - 1));
+        const double u = ((double)k - mid) / (double)d;
+        const double sinc = u == 0.0 ? 1.0 : std::sin(pi * u) / (pi * u);
+        h[(size_t)k] = w * sinc / (double)d;
+        sum += h[(size_t)k];
+    }
+    for (int64_t k = 0; k < n_taps; ++k) taps[k] = (float)(h[(size_t)k] * ((double)d / sum));
+    return SPEC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// spec_internal.h -- launchers shared between the C-ABI layer and the
+// kernel translation units.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace spec {
+
+// Largest per-CTA tile of complex elements for the one-pass kernels.
+constexpr int kTile = 8192;
+
+inline int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int ilog2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+// Phase in cycles -> 64-bit fixed-point fraction (exact wrap-around modulo
+// one cycle under unsigned multiplication).
+uint64_t cycles_to_fixed(double cycles);
+
+// ---- padded real FFT (k_fft.cu) -------------------------------------------
+struct FftPlan {
+    int H = 0;      // n_fft / 2 complex points after packing pairs of samples
+    int LZ = 0;     // length of each residue FFT (>= ceil(n/2))
+    int R = 0;      // residues H / LZ
+    int C = 0;      // CTAs (cluster size) per trace
+    int Rc = 0;     // residues per CTA
+    int F = 0;      // traces per CTA (C == 1 only)
+    int Sr = 0;     // shared-memory stride between residue blocks (float2)
+    int threads = 0;
+    size_t smem = 0;
+};
+// Returns false (with a reason) if the size needs a path this build lacks.
+bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why);
+cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
+                       float2* X, int64_t ld_X, cudaStream_t st);
+
+// ---- chirp-z by Bluestein (k_czt.cu) --------------------------------------
+struct CztTables {
+    int n = 0, m = 0, L = 0;
+    uint64_t A = 0, Bh = 0;          // frac(f1/fs), frac(step/(2 fs)) in 2^-64 cycles
+    float2* pre = nullptr;           // a[n] = e^{-j2pi(A n + Bh n^2)}, n < N
+    float2* V = nullptr;             // FFT_L(v)/L, v[m] = e^{+j2pi Bh m^2} wrapped
+    float2* post = nullptr;          // e^{-j2pi Bh k^2}, k < M
+};
+int czt_length(int64_t n, int64_t m);                 // power-of-two L >= N + M - 1
+bool czt_supported(int64_t n, int64_t m, std::string* why);
+cudaError_t czt_build_tables(const CztTables& t, cudaStream_t st);
+cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
+                       float2* X, int64_t ld_X, cudaStream_t st);
+
+// ---- Zoom FFT (k_zoom.cu) -------------------------------------------------
+struct ZoomPlan {
+    int n = 0, d = 0, n_taps = 0, K = 0, lout = 0;
+    int xlen = 0;    // extended input length (lout - 1) D + L_h
+    int rs = 0;      // polyphase row stride (floats, odd)
+    uint64_t Cn = 0; // frac(f_N / fs) in 2^-64 cycles
+    int threads = 0;
+    size_t smem = 0;
+};
+bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
+               double f2, ZoomPlan* p, std::string* why);
+cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
+                        const float* taps, float2* X, int64_t ld_X, cudaStream_t st);
+
+}  // namespace spec

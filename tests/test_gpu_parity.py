@@ -1,0 +1,189 @@
+"""Parity of the CUDA transforms with the FP64 oracle, element by element on
+the same seeded float32 inputs: relative L2 error <= 1e-5 per spectrum (the
+accuracy bar of the FP32 paths).  Sizes span several CTA tiles, clusters and
+ragged tails; the full-size batch runs in the bench's launch configuration
+and is checked on sampled traces."""
+import numpy as np
+import pytest
+
+from oracle import spec_oracle as O
+from paper_2108_03948_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2108_03948_gb300 import build
+    build.build()
+    from paper_2108_03948_gb300 import spec
+    c = spec.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2108_03948_gb300 import spec
+    return spec
+
+
+def rel_rows(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    return np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
+def traces(batch, n, seed):
+    g = np.random.default_rng(seed)
+    return g.standard_normal((batch, n)).astype(np.float32)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------- FFT ------
+
+FFT_CASES = [
+    (3, 2048, 16384), (5, 2047, 16384), (4, 1000, 8192), (3, 4097, 65536), (2, 8192, 65536),
+    (2, 16384, 131072), (2, 4096, 4096), (3, 1, 1), (3, 1, 2), (3, 2, 2), (2, 3, 4), (2, 5, 8),
+    (2, 16, 16), (2, 17, 32), (3, 33, 64), (7, 100, 128), (9, 300, 512), (5, 31, 4096), (3, 6000, 8192),
+]
+
+
+@pytest.mark.parametrize("batch,n,n_fft", FFT_CASES)
+def test_fft_parity(ctx, S, batch, n, n_fft):
+    x = traces(batch, n, 100 + n)
+    got = S.spec_fft(ctx, dev(x), 20e12, n_fft).cpu().numpy()
+    assert got.shape == (batch, n_fft // 2 + 1)
+    err = rel_rows(got, O.fft_padded(x, n_fft))
+    assert err.max() <= TOL, err
+
+
+def test_fft_thz_traces_and_strides(ctx, S):
+    x = synth.batch_traces(1, range(6))
+    base = torch.zeros((6, 2100), dtype=torch.float32, device="cuda")
+    base[:, :2048] = dev(x)
+    out = torch.full((6, 8300), float("nan"), dtype=torch.complex64, device="cuda")
+    S.spec_fft(ctx, base, 20e12, 16384, n=2048, out=out)
+    got = out[:, :8193].cpu().numpy()
+    assert rel_rows(got, O.fft_padded(x, 16384)).max() <= TOL
+    assert torch.isnan(out[:, 8193:].real).all()        # padding columns untouched
+
+
+# ---------------------------------------------------------------- CZT ------
+
+CZT_CASES = [
+    (3, 2048, 0.2e12, 2.5e12, 1024), (4, 1000, 0.1e12, 3.6e12, 256), (2, 1024, 0.8e12, 1.2e12, 512),
+    (3, 2048, 2.5e12, 0.2e12, 1024), (2, 500, 1.0e12, 1.0e12, 1), (3, 8192, 0.3e12, 3.0e12, 4096),
+    (2, 1, 0.5e12, 1.0e12, 1), (2, 3, 0.5e12, 1.0e12, 5), (5, 333, -2e12, 9.9e12, 77), (2, 64, 0.0, 19.6875e12, 64),
+]
+
+
+@pytest.mark.parametrize("batch,n,f1,f2,m", CZT_CASES)
+def test_czt_parity(ctx, S, batch, n, f1, f2, m):
+    fs = 20e12
+    x = traces(batch, n, 200 + n + m)
+    got = S.spec_czt(ctx, dev(x), fs, f1, f2, m).cpu().numpy()
+    assert got.shape == (batch, m)
+    err = rel_rows(got, O.czt(x, fs, f1, f2, m))
+    assert err.max() <= TOL, err
+
+
+def test_czt_table_cache_reuse_and_thz(ctx, S):
+    fs = 20e12
+    x = synth.batch_traces(1, range(4))
+    a = S.spec_czt(ctx, dev(x), fs, 0.2e12, 2.5e12, 1024).cpu().numpy()
+    b = S.spec_czt(ctx, dev(x), fs, 0.2e12, 2.5e12, 1024).cpu().numpy()
+    assert np.array_equal(a, b)
+    assert rel_rows(a, O.czt(x, fs, 0.2e12, 2.5e12, 1024)).max() <= TOL
+
+
+# --------------------------------------------------------------- Zoom ------
+
+ZOOM_CASES = [
+    (3, 2048, 0.2e12, 2.5e12, 4, 63, 16384), (2, 2048, 1.0e12, 1.7e12, 1, 1, 4096),
+    (3, 8192, 0.5e12, 1.5e12, 16, 127, 65536), (2, 8192, 0.5e12, 1.5e12, 4, 31, 65536),
+    (4, 30, 0.5e12, 1.5e12, 2, 5, 64), (3, 1000, 0.1e12, 2.0e12, 8, 45, 8192), (2, 2047, 3e12, 4e12, 2, 64, 16384),
+]
+
+
+@pytest.mark.parametrize("batch,n,f1,f2,d,nt,n_fft", ZOOM_CASES)
+def test_zoom_parity(ctx, S, batch, n, f1, f2, d, nt, n_fft):
+    fs = 20e12
+    x = traces(batch, n, 300 + n + d)
+    h = O.design_lowpass(nt, d).astype(np.float32)
+    got = S.spec_zoom(ctx, dev(x), fs, f1, f2, d, dev(h), n_fft).cpu().numpy()
+    assert got.shape == (batch, n_fft // d)
+    err = rel_rows(got, O.zoom(x, fs, f1, f2, d, h, n_fft))
+    assert err.max() <= TOL, err
+
+
+# ------------------------------------------------------ host-buffer path ---
+
+def test_host_buffers_match_device_path(ctx, S):
+    cfg = synth.UNIFORM[0]
+    x = synth.batch_traces(1, range(5))
+    h = O.design_lowpass(cfg.zoom_taps, cfg.zoom_d).astype(np.float32)
+    for f_host, f_dev in [
+        (lambda: S.spec_fft(ctx, x, cfg.fs, cfg.n_fft), lambda: S.spec_fft(ctx, dev(x), cfg.fs, cfg.n_fft)),
+        (lambda: S.spec_czt(ctx, x, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m),
+         lambda: S.spec_czt(ctx, dev(x), cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m)),
+        (lambda: S.spec_zoom(ctx, x, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, h, cfg.zoom_n_fft),
+         lambda: S.spec_zoom(ctx, dev(x), cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, dev(h), cfg.zoom_n_fft)),
+    ]:
+        a = f_host()
+        b = f_dev().cpu().numpy()
+        assert isinstance(a, np.ndarray)
+        assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------- errors ----
+
+def test_invalid_arguments_return_einval(ctx, S):
+    lib = S.lib()
+    x = torch.zeros((2, 64), device="cuda")
+    X = torch.zeros((2, 64), dtype=torch.complex64, device="cuda")
+    px, pX = x.data_ptr(), X.data_ptr()
+    E = S.SPEC_EINVAL
+    assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 1.0, 48, pX, 64, None) == E       # n_fft not pow2
+    assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 1.0, 32, pX, 64, None) == E       # n_fft < n
+    assert lib.spec_fft(ctx.handle, px, 2, 64, 60, 1.0, 64, pX, 64, None) == E       # ld_x < n
+    assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 0.0, 64, pX, 64, None) == E       # fs
+    assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 1.0, 64, px, 64, None) == E       # overlap
+    assert lib.spec_czt(ctx.handle, px, 2, 64, 64, 1.0, 0.0, 0.4, 0, 0, pX, 64, None) == E   # m
+    assert lib.spec_czt(ctx.handle, px, 2, 64, 64, 1.0, 0.0, 0.4, 8, 9, pX, 64, None) == E   # mode
+    assert lib.spec_czt(ctx.handle, px, 2, 64, 64, 1.0, float("nan"), 0.4, 8, 0, pX, 64, None) == E
+    h = torch.ones(8, device="cuda")
+    # L_out = ceil((64 + 7)/4) = 18 > K = 16
+    assert lib.spec_zoom(ctx.handle, px, 2, 64, 64, 1.0, 0.1, 0.2, 4, h.data_ptr(), 8, 64, pX, 64, None) == E
+    assert lib.spec_zoom(ctx.handle, px, 2, 64, 64, 1.0, 0.1, 0.2, 3, h.data_ptr(), 8, 64, pX, 64, None) == E
+    assert b"n_fft" in lib.spec_last_error(ctx.handle) or lib.spec_last_error(ctx.handle)
+    assert np.all(X.cpu().numpy() == 0)                 # nothing was written
+    # an empty batch is a no-op
+    assert lib.spec_fft(ctx.handle, px, 0, 64, 64, 1.0, 64, pX, 64, None) == S.SPEC_OK
+
+
+# ------------------------------------------------- full-size workload 1 ---
+
+def test_workload1_full_batch_sampled(ctx, S):
+    cfg = synth.UNIFORM[1]
+    x = synth.batch_traces(1, range(cfg.batch))
+    xd = dev(x)
+    h = O.design_lowpass(cfg.zoom_taps, cfg.zoom_d).astype(np.float32)
+    X = S.spec_fft(ctx, xd, cfg.fs, cfg.n_fft)
+    Z = S.spec_czt(ctx, xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m)
+    U = S.spec_zoom(ctx, xd, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, dev(h), cfg.zoom_n_fft)
+    torch.cuda.synchronize()
+    pick = [0, 1, 1000, 2047, 4094, 4095]
+    xs = x[pick]
+    assert rel_rows(X[pick].cpu().numpy(), O.fft_padded(xs, cfg.n_fft)).max() <= TOL
+    assert rel_rows(Z[pick].cpu().numpy(), O.czt(xs, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m)).max() <= TOL
+    assert rel_rows(U[pick].cpu().numpy(), O.zoom(xs, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, h,
+                                                  cfg.zoom_n_fft)).max() <= TOL
+    assert torch.isfinite(torch.view_as_real(X)).all()
+    assert torch.isfinite(torch.view_as_real(Z)).all()
+    assert torch.isfinite(torch.view_as_real(U)).all()
