@@ -1,11 +1,15 @@
 // fft_block.cuh -- device building blocks shared by the transform kernels.
 //
-// * complex helpers and in-register DFTs of size 2, 4, 8, 16;
+// * complex helpers; a complex float2 is also a packed FP32 pair, so complex
+//   additions are single add/sub.rn.f32x2 instructions;
+// * in-register DFTs of size 2, 4, 8, 16;
 // * BlockFFT: a power-of-two complex FFT executed by a group of T threads,
 //   each holding E = LF/T elements in registers.  Before and after the
 //   transform thread t holds elements t + T*i (i < E) in natural order, so
 //   loads, pointwise products and stores need no shared-memory staging; only
-//   the Stockham passes in between exchange through shared memory.
+//   the Stockham passes in between exchange through shared memory.  The
+//   inter-pass twiddles come from a table generated once in float64, laid
+//   out so that the lanes of a warp read consecutive entries;
 // * exact phases: a phase in cycles is kept as a 64-bit fixed-point fraction,
 //   so products such as (b/2) n^2 are reduced modulo one cycle exactly by
 //   integer wrap-around before any floating-point trig call.
@@ -19,14 +23,50 @@
 
 namespace spec {
 
+// ------------------------------------------------------------ packed pairs --
+__device__ __forceinline__ uint64_t pk(float2 a) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+
 // ---------------------------------------------------------------- complex --
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return sub2(a, b); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return mul2(a, make_float2(s, s)); }
 
 // multiply by e^{-j pi/2} (forward) or e^{+j pi/2} (inverse)
 template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
@@ -67,13 +107,17 @@ template <bool INV> __device__ __forceinline__ void dft2(float2& a0, float2& a1)
     a1 = t;
 }
 
+// a1, a3 = t1 -+ j d (forward) with packed ops: the swapped d times (1, -1)
+// or (-1, 1), added to t1 by one fused multiply-add (exact).
 template <bool INV> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-    float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-    float2 t2 = cadd(a1, a3), t3 = rot90<INV>(csub(a1, a3));
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    const float2 t2 = cadd(a1, a3), d = csub(a1, a3);
+    const float2 ds = make_float2(d.y, d.x);
+    const float2 p = INV ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f);
     a0 = cadd(t0, t2);
     a2 = csub(t0, t2);
-    a1 = cadd(t1, t3);
-    a3 = csub(t1, t3);
+    a1 = fma2(ds, p, t1);
+    a3 = fma2(ds, make_float2(-p.x, -p.y), t1);
 }
 
 constexpr float kS2 = 0.70710678118654752f;   // cos(pi/4)
@@ -137,38 +181,6 @@ template <int R, bool INV> __device__ __forceinline__ void dft(float2* a) {
     else if constexpr (R == 16) dft16<INV>(a);
 }
 
-// w[r] = e^{-+j 2 pi k r/S}, r = 0 .. R-1.  Two sincospif calls (w, w^4)
-// and products of depth <= 3 keep the error within a few ulp.
-template <int R, bool INV> __device__ __forceinline__ void twiddle_powers(float2* w, int k, int S) {
-    w[0] = make_float2(1.f, 0.f);
-    if constexpr (R > 1) {
-        w[1] = unit_rational<INV>(k, S);
-        if constexpr (R >= 4) { w[2] = cmul(w[1], w[1]); w[3] = cmul(w[2], w[1]); }
-        if constexpr (R >= 8) {
-            w[4] = unit_rational<INV>(4 * k, S);
-            w[5] = cmul(w[4], w[1]); w[6] = cmul(w[4], w[2]); w[7] = cmul(w[4], w[3]);
-        }
-        if constexpr (R >= 16) {
-            w[8] = cmul(w[4], w[4]);
-#pragma unroll
-            for (int r = 9; r < 12; ++r) w[r] = cmul(w[8], w[r - 8]);
-            w[12] = cmul(w[8], w[4]);
-#pragma unroll
-            for (int r = 13; r < 16; ++r) w[r] = cmul(w[12], w[r - 12]);
-        }
-    }
-}
-
-// a[r] *= w^r, w = e^{-+j 2 pi k/S}, r = 1 .. R-1.
-template <int R, bool INV> __device__ __forceinline__ void apply_twiddles(float2* a, int k, int S) {
-    if constexpr (R > 1) {
-        float2 w[R];
-        twiddle_powers<R, INV>(w, k, S);
-#pragma unroll
-        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[r]);
-    }
-}
-
 // Padded shared-memory index: one spare slot per 16 keeps the stride-R writes
 // of the first Stockham pass free of bank conflicts.
 __host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
@@ -177,11 +189,9 @@ __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
 // ---------------------------------------------------------------- BlockFFT --
-// LF-point FFT by T = LF/E threads.  Radix plan: radix-16 passes, then one
-// pass of the remaining factor (2, 4 or 8).  `s` points at padded_len(LF)
-// float2 of shared memory owned by this FFT; `t` is the thread's index in
-// [0, T).  Every thread of the CTA must call run() (it contains
-// __syncthreads), including threads whose data are dummies.
+// Radix plan of an LF-point FFT: radix-16 passes, then one pass of the
+// remaining factor (2, 4 or 8).  Pass p has NS = ns(p) (product of the
+// earlier radices) and span NS R.
 template <int LF> struct FFTShape {
     static constexpr int E = LF < 16 ? LF : 16;
     static constexpr int T = LF / E;
@@ -191,15 +201,27 @@ template <int LF> struct FFTShape {
     static constexpr int NPASS = NP16 + (REM > 1 ? 1 : 0);
     static constexpr int radix(int p) { return p < NP16 ? 16 : REM; }
     static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
+    // Twiddle table: pass p >= 1 holds w_{NS R}^{r k} at [off(p) + (r-1) NS + k],
+    // r = 1 .. R-1, k < NS; (R-1) NS = ns(p+1) - ns(p), so off(p) = ns(p) - ns(1).
+    static constexpr int tw_off(int p) { return ns(p) - ns(1); }
 };
 
+// Entries of the twiddle table of an LF-point BlockFFT: LF - 16 for LF > 16
+// (the first pass is radix-16 and needs none), 0 otherwise.
+__host__ __device__ constexpr int fft_twiddle_entries(int LF) { return LF > 16 ? LF - 16 : 0; }
+
+// LF-point FFT by T = LF/E threads.  `s` points at padded_len(LF) float2 of
+// shared memory owned by this FFT; `t` is the thread's index in [0, T);
+// `tw` is the float64-generated twiddle table of this LF (forward angles;
+// the inverse conjugates on the fly).  Every thread of the CTA must call
+// run() (it contains __syncthreads), including threads with dummy data.
 template <int LF, bool INV> struct BlockFFT {
     using S = FFTShape<LF>;
     static constexpr int E = S::E;
     static constexpr int T = S::T;
 
     template <int P>
-    static __device__ __forceinline__ void compute(float2 (&v)[E], int t) {
+    static __device__ __forceinline__ void compute(float2 (&v)[E], int t, const float2* __restrict__ tw) {
         constexpr int R = S::radix(P);
         constexpr int NS = S::ns(P);
         constexpr int NB = E / R;
@@ -209,8 +231,13 @@ template <int LF, bool INV> struct BlockFFT {
 #pragma unroll
             for (int r = 0; r < R; ++r) a[r] = v[b + r * NB];
             if constexpr (NS > 1) {
-                const int j = t + T * b;
-                apply_twiddles<R, INV>(a, j & (NS - 1), NS * R);
+                const int k = (t + T * b) & (NS - 1);
+                const float2* twp = tw + S::tw_off(P) + k;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float2 w = __ldg(twp + (r - 1) * NS);
+                    a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+                }
             }
             dft<R, INV>(a);
 #pragma unroll
@@ -240,15 +267,23 @@ template <int LF, bool INV> struct BlockFFT {
     }
 
     template <int P>
-    static __device__ __forceinline__ void passes(float2 (&v)[E], float2* s, int t) {
+    static __device__ __forceinline__ void passes(float2 (&v)[E], float2* s, int t, const float2* tw) {
         if constexpr (P < S::NPASS) {
             if constexpr (P > 0) exchange<P - 1>(v, s, t);
-            compute<P>(v, t);
-            passes<P + 1>(v, s, t);
+            compute<P>(v, t, tw);
+            passes<P + 1>(v, s, t, tw);
         }
     }
 
-    static __device__ __forceinline__ void run(float2 (&v)[E], float2* s, int t) { passes<0>(v, s, t); }
+    static __device__ __forceinline__ void run(float2 (&v)[E], float2* s, int t, const float2* tw) {
+        passes<0>(v, s, t, tw);
+    }
 };
+
+// Fill the twiddle tables of every BlockFFT size 32 .. LMAX in float64; the
+// table of size LF starts at fft_twiddle_offset(LF).
+__host__ __device__ constexpr int fft_twiddle_offset(int LF) {
+    return LF <= 32 ? 0 : fft_twiddle_offset(LF >> 1) + fft_twiddle_entries(LF >> 1);
+}
 
 }  // namespace spec

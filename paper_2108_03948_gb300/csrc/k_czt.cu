@@ -36,7 +36,8 @@ __global__ void k_czt_pre_post(float2* pre, int n, float2* post, int m, uint64_t
 
 // V = FFT_L(v)/L for the wrapped chirp kernel v; one CTA.
 template <int L>
-__global__ void __launch_bounds__(FFTShape<L>::T) k_czt_kernel_spectrum(float2* V, int n, int m, uint64_t Bh) {
+__global__ void __launch_bounds__(FFTShape<L>::T) k_czt_kernel_spectrum(float2* V, int n, int m, uint64_t Bh,
+                                                                       const float2* tw) {
     using FFT = BlockFFT<L, false>;
     constexpr int E = FFT::E, T = FFT::T;
     extern __shared__ float2 smem[];
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(FFTShape<L>::T) k_czt_kernel_spectrum(float2* 
         const uint64_t m2 = (uint64_t)(mm * mm);
         v[i] = nz ? unit_fixed_f64(Bh * m2, false) : make_float2(0.f, 0.f);
     }
-    FFT::run(v, smem, t);
+    FFT::run(v, smem, t, tw);
     const float inv = 1.0f / (float)L;
 #pragma unroll
     for (int i = 0; i < E; ++i) V[t + T * i] = cscale(v[i], inv);
@@ -71,10 +72,11 @@ struct BluesteinArgs {
     float2* X;
     int64_t ld_X;
     int F;
+    const float2* tw;
 };
 
 template <int L>
-__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256) k_czt_bluestein(BluesteinArgs a) {
+__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, FFTShape<L>::T > 256 ? 1 : 2) k_czt_bluestein(BluesteinArgs a) {
     using Fw = BlockFFT<L, false>;
     using Iv = BlockFFT<L, true>;
     constexpr int E = Fw::E, T = Fw::T;
@@ -92,10 +94,10 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256) k
         const int nn = t + T * i;
         v[i] = (live && nn < a.n) ? cscale(__ldg(&a.pre[nn]), __ldg(xr + nn)) : make_float2(0.f, 0.f);
     }
-    Fw::run(v, s, t);
+    Fw::run(v, s, t, a.tw);
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(&a.V[t + T * i]));
-    Iv::run(v, s, t);
+    Iv::run(v, s, t, a.tw);
     float2* Xr = a.X + (live ? b : 0) * a.ld_X;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256) k
 }
 
 using BsKernel = void (*)(BluesteinArgs);
-using VKernel = void (*)(float2*, int, int, uint64_t);
+using VKernel = void (*)(float2*, int, int, uint64_t, const float2*);
 
 template <int L> static void pick(int want, BsKernel* bk, VKernel* vk) {
     if (want == L) { *bk = k_czt_bluestein<L>; *vk = k_czt_kernel_spectrum<L>; }
@@ -129,7 +131,7 @@ bool czt_supported(int64_t n, int64_t m, std::string* why) {
     return true;
 }
 
-cudaError_t czt_build_tables(const CztTables& t, cudaStream_t st) {
+cudaError_t czt_build_tables(const CztTables& t, const float2* tw, cudaStream_t st) {
     BsKernel bk;
     VKernel vk;
     if (!kernels_for(t.L, &bk, &vk)) return cudaErrorInvalidValue;
@@ -141,12 +143,12 @@ cudaError_t czt_build_tables(const CztTables& t, cudaStream_t st) {
     e = cudaFuncSetAttribute(vk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int T = t.L / 16;
-    vk<<<1, T, smem, st>>>(t.V, t.n, t.m, t.Bh);
+    vk<<<1, T, smem, st>>>(t.V, t.n, t.m, t.Bh, tw);
     return cudaGetLastError();
 }
 
 cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
-                       float2* X, int64_t ld_X, cudaStream_t st) {
+                       const float2* tw, float2* X, int64_t ld_X, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     BsKernel bk;
     VKernel vk;
@@ -159,7 +161,7 @@ cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_
     if (e != cudaSuccess) return e;
     BluesteinArgs a;
     a.x = x; a.batch = batch; a.n = t.n; a.ld_x = ld_x; a.m = t.m;
-    a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F;
+    a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F; a.tw = tw;
     const int64_t grid = (batch + F - 1) / F;
     bk<<<(unsigned)grid, F * T, smem, st>>>(a);
     return cudaGetLastError();

@@ -11,8 +11,10 @@
 //  3. unpack: X[k] = (Z[k] + conj Z[H-k])/2 - j/2 w^k (Z[k] - conj Z[H-k]),
 //     w = e^{-j 2 pi/N_FFT}, for the pair (k, H - k) at once.
 // Each CTA holds <= 8192 complex points; a trace that needs more is spread
-// over a thread-block cluster whose CTAs read each other's residues through
-// distributed shared memory in step 3.
+// over a thread-block cluster.  Step 3 reads Z in natural order from shared
+// memory; in a cluster each CTA owns a contiguous chunk of Z and the others
+// reach it through distributed shared memory.  All twiddles come from tables
+// generated once in float64.
 #include <cooperative_groups.h>
 
 #include "fft_block.cuh"
@@ -27,13 +29,15 @@ struct FftArgs {
     int64_t batch;
     int n;
     int64_t ld_x;
-    int H, logR, Rc, C, F, Sr;
+    int H, logR, Rc, C, F, logChunk, trace_smem;
+    const float2* tw;     // BlockFFT<LZ> twiddles
+    const float2* tab;    // [w_H^{r t}: R x T][w_H^{r T i}: R x E][w_{2H}^k: H/2 + 1]
     float2* X;
     int64_t ld_X;
 };
 
 template <int LZ>
-__global__ void __launch_bounds__(512) k_fft_real_padded(FftArgs a) {
+__global__ void __launch_bounds__(512, 2) k_fft_real_padded(FftArgs a) {
     using FFT = BlockFFT<LZ, false>;
     constexpr int E = FFT::E;
     constexpr int T = FFT::T;
@@ -48,16 +52,17 @@ __global__ void __launch_bounds__(512) k_fft_real_padded(FftArgs a) {
     const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
     const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
     const bool live = b < a.batch;
+    const int R = 1 << a.logR;
     const int r = rank * a.Rc + rl;              // residue of this thread's FFT
     const int H = a.H;
-    float2* s = smem + (f * a.Rc + rl) * a.Sr;
+    float2* zs = smem + f * a.trace_smem;        // this trace's shared memory
+    float2* s = zs + rl * padded_len(LZ);
 
     // 1-2. packed, pre-twiddled input: v[i] = z[m] w_H^{r m}, m = t + T i.
     float2 v[E];
     {
-        float2 wi[E];
-        twiddle_powers<E, false>(wi, r * T, H);   // (w_H^{r T})^i
-        const float2 wt = unit_rational<false>(r * t, H);
+        const float2 wt = __ldg(a.tab + r * T + t);
+        const float2* wi = a.tab + R * T + r * E;
         const float* xr = a.x + (live ? b : 0) * a.ld_x;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -65,54 +70,55 @@ __global__ void __launch_bounds__(512) k_fft_real_padded(FftArgs a) {
             float re = 0.f, im = 0.f;
             if (live && 2 * m < a.n) re = __ldg(xr + 2 * m);
             if (live && 2 * m + 1 < a.n) im = __ldg(xr + 2 * m + 1);
-            v[i] = cmul(make_float2(re, im), cmul(wt, wi[i]));
+            v[i] = cmul(make_float2(re, im), cmul(wt, __ldg(wi + i)));
         }
     }
-    FFT::run(v, s, t);
+    FFT::run(v, s, t, a.tw);
 
-    // v[i] = Z[R q + r], q = t + T i.  Stage Z for the pairing step.
+    // v[i] = Z[R q + r], q = t + T i.  Stage Z in natural order; CTA c of a
+    // cluster owns Z[c chunk .. (c+1) chunk).
+    const int chunk_mask = (1 << a.logChunk) - 1;
     __syncthreads();
+    if (a.C == 1) {
 #pragma unroll
-    for (int i = 0; i < E; ++i) s[pidx(t + T * i)] = v[i];
-    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
+        for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
+        __syncthreads();
+    } else {
+        cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = ((t + T * i) << a.logR) + r;
+            float2* dst = cl.map_shared_rank(zs, k >> a.logChunk);
+            dst[pidx(k & chunk_mask)] = v[i];
+        }
+        cl.sync();
+    }
 
     // 3. unpack pairs (k, H - k), k = 0 .. H/2, split over the cluster.
-    const int R = 1 << a.logR;
     const int pairs = H / 2 + 1;
     const int per_cta = (pairs + a.C - 1) / a.C;
     const int k0 = rank * per_cta;
     const int k1 = min(pairs, k0 + per_cta);
     float2* Xr = a.X + (live ? b : 0) * a.ld_X;
-    const int N_FFT = 2 * H;
+    const float2* wp = a.tab + R * T + R * E;
     for (int k = k0 + lt; k < k1 && live; k += per_trace) {
         const int kb = (H - k) & (H - 1);
         float2 A, B;
-        {
-            const int ra = k & (R - 1), rb = kb & (R - 1);
-            const int qa = k >> a.logR, qb = kb >> a.logR;
-            const float2* sa = smem + (f * a.Rc + (ra % a.Rc)) * a.Sr;
-            const float2* sb = smem + (f * a.Rc + (rb % a.Rc)) * a.Sr;
-            if (a.C > 1) {
-                cg::cluster_group cl = cg::this_cluster();
-                sa = cl.map_shared_rank(sa, ra / a.Rc);
-                sb = cl.map_shared_rank(sb, rb / a.Rc);
-            }
-            A = sa[pidx(qa)];
-            B = sb[pidx(qb)];
+        if (a.C == 1) {
+            A = zs[pidx(k)];
+            B = zs[pidx(kb)];
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            A = cl.map_shared_rank(zs, k >> a.logChunk)[pidx(k & chunk_mask)];
+            B = cl.map_shared_rank(zs, kb >> a.logChunk)[pidx(kb & chunk_mask)];
         }
-        const float2 w = unit_rational<false>(k, N_FFT);    // e^{-j 2 pi k/N_FFT}
-        // X[k] = (A + conj B)/2 - j/2 w (A - conj B)
-        const float2 sp = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-        const float2 dm = make_float2(0.5f * (A.x - B.x), 0.5f * (A.y + B.y));
+        const float2 w = __ldg(wp + k);                     // e^{-j 2 pi k/N_FFT}
+        // X[k] = (A + conj B)/2 - j/2 w (A - conj B); X[H-k] mirrors it
+        const float2 sp = mul2(make_float2(A.x + B.x, A.y - B.y), make_float2(0.5f, 0.5f));
+        const float2 dm = mul2(make_float2(A.x - B.x, A.y + B.y), make_float2(0.5f, 0.5f));
         const float2 wd = cmul(w, dm);
         Xr[k] = make_float2(sp.x + wd.y, sp.y - wd.x);
-        if (H - k != k) {
-            // X[H-k] = (B + conj A)/2 - j/2 w' (B - conj A), w' = -conj(w)
-            const float2 sp2 = make_float2(sp.x, -sp.y);
-            const float2 dm2 = make_float2(-dm.x, dm.y);
-            const float2 wd2 = cmul(make_float2(-w.x, w.y), dm2);
-            Xr[H - k] = make_float2(sp2.x + wd2.y, sp2.y - wd2.x);
-        }
+        if (H - k != k) Xr[H - k] = make_float2(sp.x - wd.y, -sp.y - wd.x);
     }
     if (a.C > 1) cg::this_cluster().sync();   // keep shared memory alive for readers
 }
@@ -169,6 +175,8 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     p->R = (int)R;
     p->C = (int)C;
     p->Rc = (int)(R / C);
+    p->E = E;
+    p->T = T;
     const int per_trace = p->Rc * T;
     p->F = 1;
     if (C == 1) {
@@ -176,17 +184,32 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
         F = std::min<int64_t>(F, std::max<int64_t>(1, batch));
         p->F = (int)F;
     }
-    // residue stride: spread the residues of one k-run over distinct banks
-    const int base = padded_len((int)LZ);
-    const int target = R >= 16 ? 1 : (int)((16 / R) & 15);
-    p->Sr = base + (((target - base) % 16) + 16) % 16;
+    const int chunk = (int)(H / C);
+    p->trace_smem = std::max(p->Rc * padded_len((int)LZ), padded_len(chunk));
     p->threads = p->F * per_trace;
-    p->smem = (size_t)p->F * p->Rc * p->Sr * sizeof(float2);
+    p->smem = (size_t)p->F * p->trace_smem * sizeof(float2);
     return true;
 }
 
+int fft_table_entries(const FftPlan& p) { return p.R * p.T + p.R * p.E + p.H / 2 + 1; }
+
+void fft_fill_table(const FftPlan& p, float2* host) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const int64_t H = p.H;
+    auto w = [&](int64_t num, int64_t den) {     // e^{-j 2 pi num/den}, exact reduction
+        const double ang = two_pi * (double)(num % den) / (double)den;
+        return make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    };
+    float2* o = host;
+    for (int r = 0; r < p.R; ++r)
+        for (int t = 0; t < p.T; ++t) *o++ = w((int64_t)r * t, H);
+    for (int r = 0; r < p.R; ++r)
+        for (int i = 0; i < p.E; ++i) *o++ = w((int64_t)r * p.T * i, H);
+    for (int64_t k = 0; k <= H / 2; ++k) *o++ = w(k, 2 * H);
+}
+
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
-                       float2* X, int64_t ld_X, cudaStream_t st) {
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     if (p.H == 0) {   // n_fft == 1
         k_fft_len1<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(x, batch, ld_x, X, ld_X);
@@ -198,7 +221,9 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
     if (e != cudaSuccess) return e;
     FftArgs a;
     a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
-    a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = p.F; a.Sr = p.Sr;
+    a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = p.F;
+    a.logChunk = ilog2(p.H / p.C); a.trace_smem = p.trace_smem;
+    a.tw = tw; a.tab = tab;
     a.X = X; a.ld_X = ld_X;
     const int64_t groups = (batch + p.F - 1) / p.F;
     cudaLaunchConfig_t cfg = {};

@@ -11,8 +11,10 @@
 // rotation per kept output.  Only the L_out = ceil((N + L_h - 1)/D) outputs
 // that are kept are computed.  The trace sits in shared memory split by
 // phase (x[iD + p] at row p, column i) so that the lanes of a warp, which
-// compute consecutive outputs m, read consecutive words for every tap.
-// Both phases (w k and w mD) are exact 64-bit fixed-point products.
+// compute consecutive outputs m, read consecutive words for every tap; each
+// thread computes four outputs per pass over the taps, so a tap is read once
+// per four multiply-adds.  Both phases (w k and w mD) are exact 64-bit
+// fixed-point products.
 #include "fft_block.cuh"
 #include "spec_internal.h"
 
@@ -24,11 +26,14 @@ struct ZoomArgs {
     int n;
     int64_t ld_x;
     const float* taps;
-    int n_taps, d, lout, xlen, rs;
+    int n_taps, d, logd, lout, rs;
     uint64_t Cn;
+    const float2* tw;
     float2* X;
     int64_t ld_X;
 };
+
+constexpr int kZoomGroup = 4;   // outputs per thread per pass over the taps
 
 template <int K>
 __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
@@ -41,6 +46,7 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
     const int D = a.d;
 
     // shared layout: taps {g.re, g.im, offset} | polyphase x | FFT exchange
+    // (the decimated u[m] is staged in the FFT exchange area)
     float4* tap = smem4;
     float* xs = reinterpret_cast<float*>(smem4 + a.n_taps);
     float2* s = reinterpret_cast<float2*>(smem4 + a.n_taps) + (D * a.rs + 1) / 2;
@@ -55,36 +61,56 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
     }
     // extended trace xe[j] = x[j - J] (zero outside [0, N)), by phase
     const float* xr = a.x + b * a.ld_x;
-    for (int j = t; j < a.xlen; j += T) {
-        const int src = j - J;
-        const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
-        xs[(j % D) * a.rs + j / D] = xv;
+    const int total = D * a.rs;
+    if (a.logd >= 0) {
+        const int dm = D - 1;
+        for (int j = t; j < total; j += T) {
+            const int src = j - J;
+            const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
+            xs[(j & dm) * a.rs + (j >> a.logd)] = xv;
+        }
+    } else {
+        for (int j = t; j < total; j += T) {
+            const int src = j - J;
+            const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
+            xs[(j % D) * a.rs + j / D] = xv;
+        }
     }
     __syncthreads();
 
-    // FIR + decimate: thread t owns outputs m = t + T i, the FFT's input layout
-    float2 v[E];
-    const int imax = (a.lout + T - 1) / T;
+    // FIR + decimate: groups of four outputs m = t + T (4 g + u)
+    for (int m0 = t; m0 < a.lout; m0 += kZoomGroup * T) {
+        float re[kZoomGroup], im[kZoomGroup];
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-        v[i] = make_float2(0.f, 0.f);
-        if (i < imax) {
-            const int m = t + T * i;
+        for (int u = 0; u < kZoomGroup; ++u) re[u] = im[u] = 0.f;
+        const float* xm = xs + m0;
+        for (int k = 0; k < a.n_taps; ++k) {
+            const float4 g = tap[k];
+            const float* xk = xm + __float_as_int(g.z);
+#pragma unroll
+            for (int u = 0; u < kZoomGroup; ++u) {
+                const float xv = xk[u * T];
+                re[u] = fmaf(g.x, xv, re[u]);
+                im[u] = fmaf(g.y, xv, im[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kZoomGroup; ++u) {
+            const int m = m0 + u * T;
             if (m < a.lout) {
-                float re = 0.f, im = 0.f;
-                const float* xm = xs + m;
-                for (int k = 0; k < a.n_taps; ++k) {
-                    const float4 g = tap[k];
-                    const float xv = xm[__float_as_int(g.z)];
-                    re = fmaf(g.x, xv, re);
-                    im = fmaf(g.y, xv, im);
-                }
                 const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
-                v[i] = cmul(make_float2(re, im), rot);
+                s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
             }
         }
     }
-    FFT::run(v, s, t);
+    __syncthreads();
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int m = t + T * i;
+        v[i] = m < a.lout ? s[pidx(m)] : make_float2(0.f, 0.f);
+    }
+    FFT::run(v, s, t, a.tw);
     float2* Xr = a.X + b * a.ld_X;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -125,26 +151,31 @@ bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, d
         *why = "zoom: N_FFT/D above 16384 needs the multi-pass path";
         return false;
     }
-    const int64_t xlen = (lout - 1) * d + n_taps;
-    int64_t rs = (xlen + d - 1) / d + 1;
+    const int E = K < 16 ? (int)K : 16;
+    const int T = (int)(K / E);
+    // Row p holds columns 0 .. rs-1; kept outputs read columns up to
+    // (L_out - 1) + (L_h - 1)/D.  The last group of four outputs per thread
+    // may run past L_out: those reads (results discarded) stay inside the
+    // allocation, in the FFT area after the rows plus kZoomGroup T floats of
+    // slack at the end.
+    int64_t rs = (lout - 1) + (n_taps - 1) / d + 2;
     if ((rs & 1) == 0) ++rs;
     const size_t smem = (size_t)n_taps * 16 + (size_t)((d * rs + 1) / 2) * 8 +
-                        (size_t)padded_len((int)K) * 8;
+                        (size_t)padded_len((int)K) * 8 + (size_t)kZoomGroup * T * 4;
     if (smem > 200 * 1024) {
         *why = "zoom: trace plus taps exceed one CTA's shared memory; needs the multi-pass path";
         return false;
     }
     p->n = (int)n; p->d = (int)d; p->n_taps = (int)n_taps; p->K = (int)K; p->lout = (int)lout;
-    p->xlen = (int)xlen; p->rs = (int)rs;
+    p->rs = (int)rs;
     p->Cn = cycles_to_fixed(0.5 * (f1 + f2) / fs);
-    const int E = K < 16 ? (int)K : 16;
-    p->threads = (int)(K / E);
+    p->threads = T;
     p->smem = smem;
     return true;
 }
 
 cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
-                        const float* taps, float2* X, int64_t ld_X, cudaStream_t st) {
+                        const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     ZoomKernel k = zoom_kernel_for(p.K);
     if (!k) return cudaErrorInvalidValue;
@@ -152,7 +183,8 @@ cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_
     if (e != cudaSuccess) return e;
     ZoomArgs a;
     a.x = x; a.batch = batch; a.n = p.n; a.ld_x = ld_x; a.taps = taps;
-    a.n_taps = p.n_taps; a.d = p.d; a.lout = p.lout; a.xlen = p.xlen; a.rs = p.rs; a.Cn = p.Cn;
+    a.n_taps = p.n_taps; a.d = p.d; a.logd = is_pow2(p.d) ? ilog2(p.d) : -1;
+    a.lout = p.lout; a.rs = p.rs; a.Cn = p.Cn; a.tw = tw;
     a.X = X; a.ld_X = ld_X;
     k<<<(unsigned)batch, p.threads, p.smem, st>>>(a);
     return cudaGetLastError();

@@ -9,10 +9,39 @@
 #include <string>
 #include <vector>
 
+#include "fft_block.cuh"
 #include "spec.h"
 #include "spec_internal.h"
 
 namespace spec {
+
+int block_twiddle_total() { return fft_twiddle_offset(kMaxBlockFFT) + fft_twiddle_entries(kMaxBlockFFT); }
+int block_twiddle_offset(int LF) { return LF <= 16 ? 0 : fft_twiddle_offset(LF); }
+
+// Twiddles of the Stockham passes of every BlockFFT size (the layout of
+// FFTShape::tw_off): pass p >= 1 of radix R after NS points holds
+// e^{-j 2 pi r k/(NS R)} at [NS - 16 + (r-1) NS + k].  float64, exact
+// argument reduction, rounded to float.
+void block_twiddle_fill(float2* host) {
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int LF = 32; LF <= kMaxBlockFFT; LF <<= 1) {
+        float2* o = host + fft_twiddle_offset(LF);
+        const int lg = ilog2(LF), np16 = lg / 4, rem = 1 << (lg % 4);
+        const int npass = np16 + (rem > 1 ? 1 : 0);
+        int ns = 1;
+        for (int p = 0; p < npass; ++p) {
+            const int R = p < np16 ? 16 : rem;
+            if (p >= 1)
+                for (int r = 1; r < R; ++r)
+                    for (int k = 0; k < ns; ++k) {
+                        const int64_t S = (int64_t)ns * R;
+                        const double ang = two_pi * (double)(((int64_t)r * k) % S) / (double)S;
+                        o[ns - 16 + (r - 1) * ns + k] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+                    }
+            ns *= R;
+        }
+    }
+}
 
 uint64_t cycles_to_fixed(double cycles) {
     double fr = cycles - std::floor(cycles);           // [0, 1)
@@ -32,9 +61,16 @@ struct CztEntry {
     uint64_t last_use = 0;
 };
 
+struct FftEntry {
+    int H = 0, LZ = 0;
+    float2* tab = nullptr;
+};
+
 struct spec_ctx {
     int device = 0;
     std::string err;
+    float2* block_tw = nullptr;          // BlockFFT twiddles of every size
+    std::vector<FftEntry> fft;
     std::vector<CztEntry> czt;
     uint64_t tick = 0;
     void* stage[3] = {nullptr, nullptr, nullptr};   // x, X, taps
@@ -197,6 +233,20 @@ spec_status spec_ctx_create(spec_ctx** ctx, int device) {
         return SPEC_ENOMEM;
     }
     c->device = device;
+    {
+        std::vector<float2> host((size_t)block_twiddle_total());
+        block_twiddle_fill(host.data());
+        e = cudaMalloc(&c->block_tw, host.size() * sizeof(float2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->block_tw, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g_create_err = std::string("twiddle tables: ") + cudaGetErrorString(e);
+            if (c->block_tw) cudaFree(c->block_tw);
+            delete c;
+            return e == cudaErrorMemoryAllocation ? SPEC_ENOMEM : SPEC_ECUDA;
+        }
+    }
     *ctx = c;
     return SPEC_OK;
 }
@@ -210,6 +260,9 @@ void spec_ctx_destroy(spec_ctx* c) {
             if (en.mem) cudaFree(en.mem);
             if (en.ready) cudaEventDestroy(en.ready);
         }
+        for (auto& en : c->fft)
+            if (en.tab) cudaFree(en.tab);
+        if (c->block_tw) cudaFree(c->block_tw);
         for (int i = 0; i < 3; ++i)
             if (c->stage[i]) cudaFree(c->stage[i]);
         cudaGetLastError();
@@ -246,7 +299,29 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, bins, ld_X, &io)) != SPEC_OK) return s;
-    cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, io.X, ld_X, st);
+    const float2* tab = nullptr;
+    if (p.H > 0) {
+        for (auto& it : c->fft)
+            if (it.H == p.H && it.LZ == p.LZ) tab = it.tab;
+        if (!tab) {
+            FftEntry ne;
+            ne.H = p.H;
+            ne.LZ = p.LZ;
+            std::vector<float2> host((size_t)fft_table_entries(p));
+            fft_fill_table(p, host.data());
+            cudaError_t e = cudaMalloc(&ne.tab, host.size() * sizeof(float2));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(ne.tab, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                if (ne.tab) cudaFree(ne.tab);
+                return cuda_fail(c, e, "FFT tables");
+            }
+            c->fft.push_back(ne);
+            tab = ne.tab;
+        }
+    }
+    cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ), tab,
+                               io.X, ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
     return stage_out_finish(c, X, batch, bins, ld_X, st, io);
 }
@@ -292,7 +367,7 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         ne.t.post = ne.t.V + L;
         e = cudaEventCreateWithFlags(&ne.ready, cudaEventDisableTiming);
         if (e != cudaSuccess) { cudaFree(ne.mem); return cuda_fail(c, e, "event"); }
-        e = czt_build_tables(ne.t, st);
+        e = czt_build_tables(ne.t, c->block_tw + block_twiddle_offset(L), st);
         if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
         if (e != cudaSuccess) {
             cudaFree(ne.mem);
@@ -310,7 +385,7 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
-    cudaError_t e = czt_launch(en->t, io.x, batch, ld_x, io.X, ld_X, st);
+    cudaError_t e = czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
     return stage_out_finish(c, X, batch, m, ld_X, st, io);
 }
@@ -346,7 +421,8 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, K, ld_X, &io)) != SPEC_OK) return s;
-    cudaError_t e = zoom_launch(p, io.x, batch, ld_x, taps_d, io.X, ld_X, st);
+    cudaError_t e = zoom_launch(p, io.x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), io.X,
+                                ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
     return stage_out_finish(c, X, batch, K, ld_X, st, io);
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
 #include <string>
 
 namespace spec {
@@ -35,15 +37,26 @@ struct FftPlan {
     int R = 0;      // residues H / LZ
     int C = 0;      // CTAs (cluster size) per trace
     int Rc = 0;     // residues per CTA
+    int E = 0, T = 0;   // elements per thread, threads per residue FFT
     int F = 0;      // traces per CTA (C == 1 only)
-    int Sr = 0;     // shared-memory stride between residue blocks (float2)
+    int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
     size_t smem = 0;
 };
 // Returns false (with a reason) if the size needs a path this build lacks.
 bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why);
+// Per-plan twiddles (pre-twiddle factors and the unpack twiddle), float64 on
+// the host, rounded to float.
+int fft_table_entries(const FftPlan& p);
+void fft_fill_table(const FftPlan& p, float2* host);
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
-                       float2* X, int64_t ld_X, cudaStream_t st);
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st);
+
+// BlockFFT twiddle tables of every size 32 .. kMaxBlockFFT in one buffer.
+constexpr int kMaxBlockFFT = 16384;
+int block_twiddle_total();
+int block_twiddle_offset(int LF);
+void block_twiddle_fill(float2* host);
 
 // ---- chirp-z by Bluestein (k_czt.cu) --------------------------------------
 struct CztTables {
@@ -55,14 +68,13 @@ struct CztTables {
 };
 int czt_length(int64_t n, int64_t m);                 // power-of-two L >= N + M - 1
 bool czt_supported(int64_t n, int64_t m, std::string* why);
-cudaError_t czt_build_tables(const CztTables& t, cudaStream_t st);
+cudaError_t czt_build_tables(const CztTables& t, const float2* tw, cudaStream_t st);
 cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
-                       float2* X, int64_t ld_X, cudaStream_t st);
+                       const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
 
 // ---- Zoom FFT (k_zoom.cu) -------------------------------------------------
 struct ZoomPlan {
     int n = 0, d = 0, n_taps = 0, K = 0, lout = 0;
-    int xlen = 0;    // extended input length (lout - 1) D + L_h
     int rs = 0;      // polyphase row stride (floats, odd)
     uint64_t Cn = 0; // frac(f_N / fs) in 2^-64 cycles
     int threads = 0;
@@ -71,6 +83,6 @@ struct ZoomPlan {
 bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
                double f2, ZoomPlan* p, std::string* why);
 cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
-                        const float* taps, float2* X, int64_t ld_X, cudaStream_t st);
+                        const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
 
 }  // namespace spec
