@@ -138,6 +138,35 @@ SPEC_API spec_status spec_zoom(spec_ctx* ctx, const float* x, int64_t batch, int
                       const float* taps, int64_t n_taps, int64_t n_fft,
                       float* X, int64_t ld_X, void* stream);
 
+/*
+ * spec_czt without any device allocation (the paper has no counterpart;
+ * this is a deployment variant of spec_czt).
+ *
+ * For callers that cannot allocate device memory: code whose device memory
+ * is owned by another allocator (a framework's caching pool that has
+ * reserved it), real-time loops that must not call cudaMalloc (it may
+ * synchronise the device and has unbounded latency), plug-ins handed
+ * buffers but no allocator.  It needs no context.
+ *
+ * Same transform, arguments and accuracy as spec_czt in Bluestein mode,
+ * except:
+ *   - x and X must be device pointers (SPEC_EINVAL otherwise);
+ *   - N + M - 1 <= 8192, else SPEC_EUNSUPPORTED before any launch;
+ *   - working memory is one file-scope device array of about 320 KiB (FFT
+ *     twiddles, chirp tables and the chirp kernel's spectrum) that every
+ *     GPU loading the library keeps until the process exits;
+ *   - the first call on each device (the current device) fetches the
+ *     array's device address, fills its twiddles and synchronises `stream`;
+ *     make that first call before any stream capture;
+ *   - every call rewrites the chirp tables in that shared array, so calls
+ *     that overlap on the GPU (e.g. on two streams) race: order them on one
+ *     stream.
+ * Returns SPEC_ECUDA if a CUDA call fails.
+ */
+SPEC_API spec_status spec_czt_static(const float* x, int64_t batch, int64_t n, int64_t ld_x,
+                                     double fs, double f1, double f2, int64_t m,
+                                     float* X, int64_t ld_X, void* stream);
+
 /* ---- host-only helpers (pure functions, no CUDA calls) ----------------- */
 
 /* Zeros to append to an N_FFT-sample record so that its bin spacing shrinks

@@ -26,7 +26,7 @@ _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "
            SPEC_EUNSUPPORTED: "SPEC_EUNSUPPORTED", SPEC_ETIMEOUT: "SPEC_ETIMEOUT"}
 
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
-           "spec_fft", "spec_czt", "spec_zoom",
+           "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
 
 _lib = None
@@ -61,6 +61,8 @@ def lib():
     L.spec_czt.restype = C.c_int
     L.spec_zoom.argtypes = [vp, fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, i64, fp, i64, vp]
     L.spec_zoom.restype = C.c_int
+    L.spec_czt_static.argtypes = [fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, vp]
+    L.spec_czt_static.restype = C.c_int
     L.spec_zeros_for_delta.argtypes = [dbl, i64, dbl]
     L.spec_zeros_for_delta.restype = i64
     L.spec_m_for_resolution.argtypes = [dbl, dbl, dbl, i64]
