@@ -100,24 +100,96 @@ __device__ __forceinline__ float2 unit_fixed(uint64_t ph, bool negative) {
     return negative ? make_float2(re, -im) : make_float2(re, im);
 }
 
+// ------------------------------------------------- two-lane complex pairs --
+// C2 holds two independent complex numbers a and b as packed FP32 pairs:
+// re = (a.x, b.x), im = (a.y, b.y).  Every operation below is one packed
+// instruction per component, so a C2 costs the instructions of one complex.
+struct C2 {
+    float2 re, im;
+};
+__device__ __forceinline__ C2 c2(float2 a, float2 b) { return C2{make_float2(a.x, b.x), make_float2(a.y, b.y)}; }
+__device__ __forceinline__ float2 lane_a(C2 v) { return make_float2(v.re.x, v.im.x); }
+__device__ __forceinline__ float2 lane_b(C2 v) { return make_float2(v.re.y, v.im.y); }
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return sub2(a, b); }
+__device__ __forceinline__ C2 vadd(C2 a, C2 b) { return C2{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ C2 vsub(C2 a, C2 b) { return C2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ C2 vneg(C2 a) {
+    return C2{mul2(a.re, make_float2(-1.f, -1.f)), mul2(a.im, make_float2(-1.f, -1.f))};
+}
+
+// o1 = t1 - j d, o3 = t1 + j d (forward); the inverse swaps them
+template <bool INV> __device__ __forceinline__ void jpair(float2 t1, float2 d, float2& o1, float2& o3) {
+    const float2 ds = make_float2(d.y, d.x);
+    const float2 p = INV ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f);
+    o1 = fma2(ds, p, t1);
+    o3 = fma2(ds, make_float2(-p.x, -p.y), t1);
+}
+template <bool INV> __device__ __forceinline__ void jpair(C2 t1, C2 d, C2& o1, C2& o3) {
+    const C2 m = C2{add2(t1.re, d.im), sub2(t1.im, d.re)};   // t1 - j d
+    const C2 p = C2{sub2(t1.re, d.im), add2(t1.im, d.re)};   // t1 + j d
+    o1 = INV ? p : m;
+    o3 = INV ? m : p;
+}
+
+// multiply by e^{-j pi/2} (forward) or e^{+j pi/2} (inverse)
+template <bool INV> __device__ __forceinline__ C2 rot90(C2 a) {
+    return INV ? C2{vneg(a).im, a.re} : C2{a.im, vneg(a).re};
+}
+
+// multiply by the constant c + j w
+__device__ __forceinline__ float2 mulk(float2 a, float c, float w) {
+    return make_float2(fmaf(a.x, c, -a.y * w), fmaf(a.x, w, a.y * c));
+}
+__device__ __forceinline__ C2 mulk(C2 a, float c, float w) {
+    return C2{fma2(a.re, make_float2(c, c), mul2(a.im, make_float2(-w, -w))),
+              fma2(a.re, make_float2(w, w), mul2(a.im, make_float2(c, c)))};
+}
+
+// Table twiddles: float2 w = c + j s (the forward twiddle) for both lane
+// types; the inverse uses conj(w).  For C2 the packed pairs (c, c) and
+// (s, s) are built in registers, keeping the tables small enough for L1.
+template <class V> struct TwEntry;
+template <> struct TwEntry<float2> { using type = float2; };
+template <> struct TwEntry<C2> { using type = float2; };
+
+template <bool INV> __device__ __forceinline__ float2 mul_tw(float2 a, float2 w) {
+    return INV ? cmulc(a, w) : cmul(a, w);
+}
+template <bool INV> __device__ __forceinline__ C2 mul_tw(C2 a, float2 w) {
+    const float2 cc = make_float2(w.x, w.x), ss = make_float2(w.y, w.y);
+    const float2 rc = mul2(a.re, cc), ic = mul2(a.im, cc);
+    if (INV) return C2{fma2(a.im, ss, rc), sub2(ic, mul2(a.re, ss))};
+    return C2{sub2(rc, mul2(a.im, ss)), fma2(a.re, ss, ic)};
+}
+
+// shared-memory element of a lane type
+__device__ __forceinline__ void sts(float2* s, int i, float2 v) { s[i] = v; }
+__device__ __forceinline__ float2 lds(const float2* s, int i, float2*) { return s[i]; }
+__device__ __forceinline__ void sts(float4* s, int i, C2 v) { s[i] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+__device__ __forceinline__ C2 lds(const float4* s, int i, C2*) {
+    const float4 q = s[i];
+    return C2{make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+template <class V> struct SmemT;
+template <> struct SmemT<float2> { using type = float2; };
+template <> struct SmemT<C2> { using type = float4; };
+
 // ------------------------------------------------------ in-register DFTs --
-template <bool INV> __device__ __forceinline__ void dft2(float2& a0, float2& a1) {
-    float2 t = csub(a0, a1);
-    a0 = cadd(a0, a1);
+template <bool INV, class V> __device__ __forceinline__ void dft2(V& a0, V& a1) {
+    V t = vsub(a0, a1);
+    a0 = vadd(a0, a1);
     a1 = t;
 }
 
-// a1, a3 = t1 -+ j d (forward) with packed ops: the swapped d times (1, -1)
-// or (-1, 1), added to t1 by one fused multiply-add (exact).
-template <bool INV> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-    const float2 t2 = cadd(a1, a3), d = csub(a1, a3);
-    const float2 ds = make_float2(d.y, d.x);
-    const float2 p = INV ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f);
-    a0 = cadd(t0, t2);
-    a2 = csub(t0, t2);
-    a1 = fma2(ds, p, t1);
-    a3 = fma2(ds, make_float2(-p.x, -p.y), t1);
+template <bool INV, class V> __device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
+    const V t0 = vadd(a0, a2), t1 = vsub(a0, a2);
+    const V t2 = vadd(a1, a3), d = vsub(a1, a3);
+    a0 = vadd(t0, t2);
+    a2 = vsub(t0, t2);
+    jpair<INV>(t1, d, a1, a3);
 }
 
 constexpr float kS2 = 0.70710678118654752f;   // cos(pi/4)
@@ -125,11 +197,11 @@ constexpr float kC8 = 0.92387953251128674f;   // cos(pi/8)
 constexpr float kS8 = 0.38268343236508978f;   // sin(pi/8)
 
 // multiply by w16^P = e^{-j 2 pi P/16} (forward) or its conjugate (inverse)
-template <int P, bool INV> __device__ __forceinline__ float2 tw16(float2 a) {
+template <int P, bool INV, class V> __device__ __forceinline__ V tw16(V a) {
     constexpr int Q = P & 15;
     if constexpr (Q == 0) return a;
     else if constexpr (Q == 4) return rot90<INV>(a);
-    else if constexpr (Q == 8) return make_float2(-a.x, -a.y);
+    else if constexpr (Q == 8) return vneg(a);
     else if constexpr (Q == 12) return rot90<!INV>(a);
     else {
         // cos / sin of 2 pi Q/16 for Q in {1,2,3,5,6,7,9,10,11,13,14,15}
@@ -138,24 +210,23 @@ template <int P, bool INV> __device__ __forceinline__ float2 tw16(float2 a) {
         constexpr float s = (Q == 1 || Q == 7) ? kS8 : (Q == 2 || Q == 6) ? kS2 : (Q == 3 || Q == 5) ? kC8
                           : (Q == 9 || Q == 15) ? -kS8 : (Q == 10 || Q == 14) ? -kS2 : -kC8;
         // forward: e^{-j theta} = (c, -s); inverse: (c, s)
-        constexpr float wi = INV ? s : -s;
-        return make_float2(fmaf(a.x, c, -a.y * wi), fmaf(a.x, wi, a.y * c));
+        return mulk(a, c, INV ? s : -s);
     }
 }
 
-template <bool INV> __device__ __forceinline__ void dft8(float2* a) {
+template <bool INV, class V> __device__ __forceinline__ void dft8(V* a) {
     dft4<INV>(a[0], a[2], a[4], a[6]);
     dft4<INV>(a[1], a[3], a[5], a[7]);
-    float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
-    float2 o0 = a[1], o1 = tw16<2, INV>(a[3]), o2 = tw16<4, INV>(a[5]), o3 = tw16<6, INV>(a[7]);
-    a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
-    a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
-    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
-    a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+    V e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    V o0 = a[1], o1 = tw16<2, INV>(a[3]), o2 = tw16<4, INV>(a[5]), o3 = tw16<6, INV>(a[7]);
+    a[0] = vadd(e0, o0); a[4] = vsub(e0, o0);
+    a[1] = vadd(e1, o1); a[5] = vsub(e1, o1);
+    a[2] = vadd(e2, o2); a[6] = vsub(e2, o2);
+    a[3] = vadd(e3, o3); a[7] = vsub(e3, o3);
 }
 
 // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.
-template <bool INV> __device__ __forceinline__ void dft16(float2* a) {
+template <bool INV, class V> __device__ __forceinline__ void dft16(V* a) {
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
     // slot 4 k1 + n2 now holds B[n2][k1]; twiddle by w16^{n2 k1}
@@ -165,7 +236,7 @@ template <bool INV> __device__ __forceinline__ void dft16(float2* a) {
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
     // slot 4 k1 + k2 holds X[k1 + 4 k2]: transpose the 4x4 (register renaming)
-    float2 t;
+    V t;
     t = a[1]; a[1] = a[4]; a[4] = t;
     t = a[2]; a[2] = a[8]; a[8] = t;
     t = a[3]; a[3] = a[12]; a[12] = t;
@@ -174,7 +245,7 @@ template <bool INV> __device__ __forceinline__ void dft16(float2* a) {
     t = a[11]; a[11] = a[14]; a[14] = t;
 }
 
-template <int R, bool INV> __device__ __forceinline__ void dft(float2* a) {
+template <int R, bool INV, class V> __device__ __forceinline__ void dft(V* a) {
     if constexpr (R == 2) dft2<INV>(a[0], a[1]);
     else if constexpr (R == 4) dft4<INV>(a[0], a[1], a[2], a[3]);
     else if constexpr (R == 8) dft8<INV>(a);
@@ -210,33 +281,44 @@ template <int LF> struct FFTShape {
 // (the first pass is radix-16 and needs none), 0 otherwise.
 __host__ __device__ constexpr int fft_twiddle_entries(int LF) { return LF > 16 ? LF - 16 : 0; }
 
-// LF-point FFT by T = LF/E threads.  `s` points at padded_len(LF) float2 of
-// shared memory owned by this FFT; `t` is the thread's index in [0, T);
-// `tw` is the float64-generated twiddle table of this LF (forward angles;
-// the inverse conjugates on the fly).  Every thread of the CTA must call
-// run() (it contains __syncthreads), including threads with dummy data.
-template <int LF, bool INV> struct BlockFFT {
+// LF-point FFT by T = LF/E threads, on lane type V (float2: one FFT per
+// thread group; C2: two FFTs with the same twiddles, one per packed lane).
+// `s` points at padded_len(LF) shared elements (SmemT<V>) owned by this FFT;
+// `t` is the thread's index in [0, T); `tw` is the float64-generated twiddle
+// table of this LF (TwEntry<V>; forward angles, the inverse conjugates on
+// the fly).  Every thread of the CTA must call run() (it contains
+// __syncthreads), including threads with dummy data.
+#ifndef SPEC_TW_CHUNK
+#define SPEC_TW_CHUNK 8
+#endif
+constexpr int kTwChunk = SPEC_TW_CHUNK;   // twiddles loaded per compiler fence
+
+template <int LF, bool INV, class V = float2> struct BlockFFT {
     using S = FFTShape<LF>;
+    using TW = typename TwEntry<V>::type;
+    using SM = typename SmemT<V>::type;
     static constexpr int E = S::E;
     static constexpr int T = S::T;
 
     template <int P>
-    static __device__ __forceinline__ void compute(float2 (&v)[E], int t, const float2* __restrict__ tw) {
+    static __device__ __forceinline__ void compute(V (&v)[E], int t, const TW* __restrict__ tw) {
         constexpr int R = S::radix(P);
         constexpr int NS = S::ns(P);
         constexpr int NB = E / R;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            float2 a[R];
+            V a[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) a[r] = v[b + r * NB];
             if constexpr (NS > 1) {
                 const int k = (t + T * b) & (NS - 1);
-                const float2* twp = tw + S::tw_off(P) + k;
+                const TW* twp = tw + S::tw_off(P) + k;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = __ldg(twp + (r - 1) * NS);
-                    a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+                    // a compiler-only fence every kTwChunk twiddles keeps the
+                    // loads from all being hoisted (register pressure)
+                    if (r % kTwChunk == 0) asm volatile("" ::: "memory");
+                    a[r] = mul_tw<INV>(a[r], __ldg(twp + (r - 1) * NS));
                 }
             }
             dft<R, INV>(a);
@@ -248,7 +330,7 @@ template <int LF, bool INV> struct BlockFFT {
     // Write the outputs of pass P to their Stockham positions, then read the
     // thread's next inputs t + T i.
     template <int P>
-    static __device__ __forceinline__ void exchange(float2 (&v)[E], float2* s, int t) {
+    static __device__ __forceinline__ void exchange(V (&v)[E], SM* s, int t) {
         constexpr int R = S::radix(P);
         constexpr int NS = S::ns(P);
         constexpr int NB = E / R;
@@ -259,15 +341,15 @@ template <int LF, bool INV> struct BlockFFT {
             const int k = j & (NS - 1);
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[pidx(base + r * NS)] = v[b + r * NB];
+            for (int r = 0; r < R; ++r) sts(s, pidx(base + r * NS), v[b + r * NB]);
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = s[pidx(t + T * i)];
+        for (int i = 0; i < E; ++i) v[i] = lds(s, pidx(t + T * i), (V*)nullptr);
     }
 
     template <int P>
-    static __device__ __forceinline__ void passes(float2 (&v)[E], float2* s, int t, const float2* tw) {
+    static __device__ __forceinline__ void passes(V (&v)[E], SM* s, int t, const TW* tw) {
         if constexpr (P < S::NPASS) {
             if constexpr (P > 0) exchange<P - 1>(v, s, t);
             compute<P>(v, t, tw);
@@ -275,7 +357,7 @@ template <int LF, bool INV> struct BlockFFT {
         }
     }
 
-    static __device__ __forceinline__ void run(float2 (&v)[E], float2* s, int t, const float2* tw) {
+    static __device__ __forceinline__ void run(V (&v)[E], SM* s, int t, const TW* tw) {
         passes<0>(v, s, t, tw);
     }
 };

@@ -97,12 +97,70 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, F
     Fw::run(v, s, t, a.tw);
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(&a.V[t + T * i]));
-    Iv::run(v, s, t, a.tw);
+    int ti = t;                        // opaque copy: see k_czt_bluestein2
+    asm volatile("" : "+r"(ti));
+    Iv::run(v, s, ti, a.tw);
     float2* Xr = a.X + (live ? b : 0) * a.ld_X;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int k = t + T * i;
         if (live && k < a.m) Xr[k] = cmul(v[i], __ldg(&a.post[k]));
+    }
+}
+
+// Two-lane variant: traces 2p and 2p+1 ride in the two packed lanes of a C2,
+// so every table value (pre, V, post, twiddles) is loaded once per pair and
+// each FFT instruction serves both traces.
+template <int L>
+__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, FFTShape<L>::T > 256 ? 1 : 2)
+    k_czt_bluestein2(BluesteinArgs a) {
+    using Fw = BlockFFT<L, false, C2>;
+    using Iv = BlockFFT<L, true, C2>;
+    constexpr int E = Fw::E, T = Fw::T;
+    extern __shared__ float4 smem4[];
+    const int f = threadIdx.x / T;
+    const int t = threadIdx.x - f * T;
+    const int64_t b0 = ((int64_t)blockIdx.x * a.F + f) * 2, b1 = b0 + 1;
+    const bool live0 = b0 < a.batch, live1 = b1 < a.batch;
+    float4* s = smem4 + f * padded_len(L);
+    const float* x0 = a.x + (live0 ? b0 : 0) * a.ld_x;
+    const float* x1 = a.x + (live1 ? b1 : 0) * a.ld_x;
+
+    C2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int nn = t + T * i;
+        if (i % 4 == 0) asm volatile("" ::: "memory");
+        if (nn < a.n) {
+            const float2 p = __ldg(&a.pre[nn]);
+            const float2 xx = make_float2(live0 ? __ldg(x0 + nn) : 0.f, live1 ? __ldg(x1 + nn) : 0.f);
+            v[i] = C2{mul2(make_float2(p.x, p.x), xx), mul2(make_float2(p.y, p.y), xx)};
+        } else {
+            v[i] = C2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        }
+    }
+    Fw::run(v, s, t, a.tw);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        if (i % 4 == 0) asm volatile("" ::: "memory");   // bound the hoisted float4 loads
+        v[i] = mul_tw<false>(v[i], __ldg(&a.V[t + T * i]));
+    }
+    // an opaque copy of t: the inverse FFT recomputes its shared-memory
+    // addresses instead of keeping the forward FFT's alive (register pressure)
+    int ti = t;
+    asm volatile("" : "+r"(ti));
+    Iv::run(v, s, ti, a.tw);
+    float2* X0 = a.X + (live0 ? b0 : 0) * a.ld_X;
+    float2* X1 = a.X + (live1 ? b1 : 0) * a.ld_X;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = t + T * i;
+        if (i % 4 == 0) asm volatile("" ::: "memory");
+        if (k < a.m) {
+            const C2 r = mul_tw<false>(v[i], __ldg(&a.post[k]));
+            if (live0) X0[k] = lane_a(r);
+            if (live1) X1[k] = lane_b(r);
+        }
     }
 }
 
@@ -163,6 +221,40 @@ cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_
     a.x = x; a.batch = batch; a.n = t.n; a.ld_x = ld_x; a.m = t.m;
     a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F; a.tw = tw;
     const int64_t grid = (batch + F - 1) / F;
+    bk<<<(unsigned)grid, F * T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int L> static void pick2(int want, BsKernel* bk) {
+    if (want == L) *bk = k_czt_bluestein2<L>;
+}
+
+static bool kernel2_for(int L, BsKernel* bk) {
+    *bk = nullptr;
+    pick2<16>(L, bk); pick2<32>(L, bk); pick2<64>(L, bk); pick2<128>(L, bk); pick2<256>(L, bk);
+    pick2<512>(L, bk); pick2<1024>(L, bk); pick2<2048>(L, bk); pick2<4096>(L, bk); pick2<8192>(L, bk);
+    return *bk != nullptr;
+}
+
+bool czt_dual_ok(int L) { return L >= 16 && L <= 8192; }
+
+cudaError_t czt_launch2(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
+                        const float2* tw, float2* X, int64_t ld_X, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    BsKernel bk;
+    if (!kernel2_for(t.L, &bk)) return cudaErrorInvalidValue;
+    const int T = t.L / 16;
+    const int64_t pairs = (batch + 1) / 2;
+    int F = std::max(1, 256 / T);
+    F = (int)std::min<int64_t>(F, pairs);
+    const size_t smem = (size_t)F * padded_len(t.L) * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    BluesteinArgs a = {};
+    a.x = x; a.batch = batch; a.n = t.n; a.ld_x = ld_x; a.m = t.m;
+    a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F;
+    a.tw = tw;
+    const int64_t grid = (pairs + F - 1) / F;
     bk<<<(unsigned)grid, F * T, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -123,6 +123,101 @@ __global__ void __launch_bounds__(512, 2) k_fft_real_padded(FftArgs a) {
     if (a.C > 1) cg::this_cluster().sync();   // keep shared memory alive for readers
 }
 
+// Two-lane variant: each thread carries residues ra and ra + Rc/2 of one
+// trace as the two packed lanes of a C2, so the packed input is read once per
+// pair and the FFT arithmetic and twiddle loads are shared by both residues.
+// Same staging and unpack as k_fft_real_padded.
+template <int LZ>
+__global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
+    using FFT = BlockFFT<LZ, false, C2>;
+    constexpr int E = FFT::E;
+    constexpr int T = FFT::T;
+    extern __shared__ float4 smem4[];
+
+    const int G = a.Rc >> 1;                     // residue pairs per CTA per trace
+    const int per_trace = G * T;
+    const int tid = threadIdx.x;
+    const int f = tid / per_trace;
+    const int lt = tid - f * per_trace;
+    const int gl = lt / T;
+    const int t = lt - gl * T;
+    const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
+    const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
+    const bool live = b < a.batch;
+    const int R = 1 << a.logR;
+    const int ra = rank * a.Rc + gl;             // lane a residue
+    const int rb = ra + G;                       // lane b residue
+    const int H = a.H;
+    float2* zs = reinterpret_cast<float2*>(smem4) + f * a.trace_smem;
+    float4* s = reinterpret_cast<float4*>(zs) + gl * padded_len(LZ);
+
+    C2 v[E];
+    {
+        const float2 wta = __ldg(a.tab + ra * T + t), wtb = __ldg(a.tab + rb * T + t);
+        const float2* wia = a.tab + R * T + ra * E;
+        const float2* wib = a.tab + R * T + rb * E;
+        const float* xr = a.x + (live ? b : 0) * a.ld_x;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float re = 0.f, im = 0.f;
+            if (live && 2 * m < a.n) re = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < a.n) im = __ldg(xr + 2 * m + 1);
+            const float2 z = make_float2(re, im);
+            v[i] = c2(cmul(z, cmul(wta, __ldg(wia + i))), cmul(z, cmul(wtb, __ldg(wib + i))));
+        }
+    }
+    FFT::run(v, s, t, a.tw);
+
+    const int chunk_mask = (1 << a.logChunk) - 1;
+    __syncthreads();
+    if (a.C == 1) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int q = (t + T * i) << a.logR;
+            zs[pidx(q + ra)] = lane_a(v[i]);
+            zs[pidx(q + rb)] = lane_b(v[i]);
+        }
+        __syncthreads();
+    } else {
+        cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int q = (t + T * i) << a.logR;
+            const int ka = q + ra, kb = q + rb;
+            cl.map_shared_rank(zs, ka >> a.logChunk)[pidx(ka & chunk_mask)] = lane_a(v[i]);
+            cl.map_shared_rank(zs, kb >> a.logChunk)[pidx(kb & chunk_mask)] = lane_b(v[i]);
+        }
+        cl.sync();
+    }
+
+    const int pairs = H / 2 + 1;
+    const int per_cta = (pairs + a.C - 1) / a.C;
+    const int k0 = rank * per_cta;
+    const int k1 = min(pairs, k0 + per_cta);
+    float2* Xr = a.X + (live ? b : 0) * a.ld_X;
+    const float2* wp = a.tab + R * T + R * E;
+    for (int k = k0 + lt; k < k1 && live; k += per_trace) {
+        const int kb = (H - k) & (H - 1);
+        float2 A, B;
+        if (a.C == 1) {
+            A = zs[pidx(k)];
+            B = zs[pidx(kb)];
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            A = cl.map_shared_rank(zs, k >> a.logChunk)[pidx(k & chunk_mask)];
+            B = cl.map_shared_rank(zs, kb >> a.logChunk)[pidx(kb & chunk_mask)];
+        }
+        const float2 w = __ldg(wp + k);
+        const float2 sp = mul2(make_float2(A.x + B.x, A.y - B.y), make_float2(0.5f, 0.5f));
+        const float2 dm = mul2(make_float2(A.x - B.x, A.y + B.y), make_float2(0.5f, 0.5f));
+        const float2 wd = cmul(w, dm);
+        Xr[k] = make_float2(sp.x + wd.y, sp.y - wd.x);
+        if (H - k != k) Xr[H - k] = make_float2(sp.x - wd.y, -sp.y - wd.x);
+    }
+    if (a.C > 1) cg::this_cluster().sync();
+}
+
 // n_fft == 1: the single bin is x[0].
 __global__ void k_fft_len1(const float* x, int64_t batch, int64_t ld_x, float2* X, int64_t ld_X) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,6 +225,21 @@ __global__ void k_fft_len1(const float* x, int64_t batch, int64_t ld_x, float2* 
 }
 
 using FftKernel = void (*)(FftArgs);
+
+static FftKernel fft_kernel2_for(int LZ) {
+    switch (LZ) {
+        case 16: return k_fft_real_padded2<16>;
+        case 32: return k_fft_real_padded2<32>;
+        case 64: return k_fft_real_padded2<64>;
+        case 128: return k_fft_real_padded2<128>;
+        case 256: return k_fft_real_padded2<256>;
+        case 512: return k_fft_real_padded2<512>;
+        case 1024: return k_fft_real_padded2<1024>;
+        case 2048: return k_fft_real_padded2<2048>;
+        case 4096: return k_fft_real_padded2<4096>;
+        default: return nullptr;
+    }
+}
 
 static FftKernel fft_kernel_for(int LZ) {
     switch (LZ) {
@@ -177,7 +287,8 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     p->Rc = (int)(R / C);
     p->E = E;
     p->T = T;
-    const int per_trace = p->Rc * T;
+    p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096;
+    const int per_trace = p->dual ? (p->Rc / 2) * T : p->Rc * T;
     p->F = 1;
     if (C == 1) {
         int64_t F = std::max<int64_t>(1, 256 / per_trace);
@@ -186,6 +297,7 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     }
     const int chunk = (int)(H / C);
     p->trace_smem = std::max(p->Rc * padded_len((int)LZ), padded_len(chunk));
+    p->trace_smem += p->trace_smem & 1;       // keep float4 views 16-byte aligned
     p->threads = p->F * per_trace;
     p->smem = (size_t)p->F * p->trace_smem * sizeof(float2);
     return true;
@@ -209,27 +321,34 @@ void fft_fill_table(const FftPlan& p, float2* host) {
 }
 
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
-                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st) {
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
+                       int lanes) {
     if (batch == 0) return cudaSuccess;
     if (p.H == 0) {   // n_fft == 1
         k_fft_len1<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(x, batch, ld_x, X, ld_X);
         return cudaGetLastError();
     }
-    FftKernel k = fft_kernel_for(p.LZ);
+    const bool dual = p.dual && lanes != 1;
+    FftKernel k = dual ? fft_kernel2_for(p.LZ) : fft_kernel_for(p.LZ);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-    if (e != cudaSuccess) return e;
     FftArgs a;
     a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
-    a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = p.F;
+    a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C;
     a.logChunk = ilog2(p.H / p.C); a.trace_smem = p.trace_smem;
     a.tw = tw; a.tab = tab;
     a.X = X; a.ld_X = ld_X;
-    const int64_t groups = (batch + p.F - 1) / p.F;
+    const int per_trace = dual ? (p.Rc / 2) * p.T : p.Rc * p.T;
+    int F = 1;
+    if (p.C == 1) F = (int)std::min<int64_t>(std::max(1, 256 / per_trace), std::max<int64_t>(1, batch));
+    a.F = F;
+    const size_t smem = (size_t)F * p.trace_smem * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t groups = (batch + F - 1) / F;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(groups * p.C));
-    cfg.blockDim = dim3(p.threads);
-    cfg.dynamicSmemBytes = p.smem;
+    cfg.blockDim = dim3(F * per_trace);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     cfg.attrs = attr;

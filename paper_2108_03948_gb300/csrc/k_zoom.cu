@@ -119,7 +119,107 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
     }
 }
 
+// Two-lane variant: traces 2p and 2p+1 share one CTA.  Their samples sit
+// side by side in shared memory (one float2 per polyphase slot), so each tap
+// -- stored duplicated as (g.re, g.re, g.im, g.im) -- feeds both traces with
+// two packed multiply-adds, and the FFT runs on packed pairs.
+template <int K>
+__global__ void __launch_bounds__(FFTShape<K>::T) k_zoom2(ZoomArgs a) {
+    using FFT = BlockFFT<K, false, C2>;
+    constexpr int E = FFT::E, T = FFT::T;
+    extern __shared__ float4 smem4[];
+    const int t = threadIdx.x;
+    const int64_t b0 = 2 * (int64_t)blockIdx.x, b1 = b0 + 1;
+    const bool live1 = b1 < a.batch;
+    const int J = a.n_taps - 1;
+    const int D = a.d;
+
+    // shared layout: taps (g.re, g.re, g.im, g.im) | polyphase x pairs |
+    // FFT exchange (float4) | tap offsets (int) | slack
+    float4* tap = smem4;
+    float2* xs = reinterpret_cast<float2*>(smem4 + a.n_taps);
+    float4* s = smem4 + a.n_taps + (D * a.rs + 1) / 2;
+    int* toff = reinterpret_cast<int*>(s + padded_len(K));
+
+    for (int k = t; k < a.n_taps; k += T) {
+        const float h = __ldg(a.taps + k);
+        const float2 e = unit_fixed(a.Cn * (uint64_t)k, false);
+        const int q = J - k;
+        tap[k] = make_float4(h * e.x, h * e.x, h * e.y, h * e.y);
+        toff[k] = (q % D) * a.rs + q / D;
+    }
+    const float* x0 = a.x + b0 * a.ld_x;
+    const float* x1 = a.x + (live1 ? b1 : b0) * a.ld_x;
+    const int total = D * a.rs;
+    for (int j = t; j < total; j += T) {
+        const int src = j - J;
+        const bool in = src >= 0 && src < a.n;
+        const float2 xv = make_float2(in ? __ldg(x0 + src) : 0.f, (in && live1) ? __ldg(x1 + src) : 0.f);
+        const int slot = a.logd >= 0 ? (j & (D - 1)) * a.rs + (j >> a.logd) : (j % D) * a.rs + j / D;
+        xs[slot] = xv;
+    }
+    __syncthreads();
+
+    for (int m0 = t; m0 < a.lout; m0 += kZoomGroup * T) {
+        float2 re[kZoomGroup], im[kZoomGroup];
+#pragma unroll
+        for (int u = 0; u < kZoomGroup; ++u) re[u] = im[u] = make_float2(0.f, 0.f);
+        const float2* xm = xs + m0;
+        for (int k = 0; k < a.n_taps; ++k) {
+            const float4 g = tap[k];
+            const float2* xk = xm + toff[k];
+            const float2 gr = make_float2(g.x, g.y), gi = make_float2(g.z, g.w);
+#pragma unroll
+            for (int u = 0; u < kZoomGroup; ++u) {
+                const float2 xv = xk[u * T];
+                re[u] = fma2(gr, xv, re[u]);
+                im[u] = fma2(gi, xv, im[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kZoomGroup; ++u) {
+            const int m = m0 + u * T;
+            if (m < a.lout) {
+                const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
+                sts(s, pidx(m), mul_tw<false>(C2{re[u], im[u]}, rot));
+            }
+        }
+    }
+    __syncthreads();
+    C2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int m = t + T * i;
+        v[i] = m < a.lout ? lds(s, pidx(m), (C2*)nullptr) : C2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    }
+    FFT::run(v, s, t, a.tw);
+    float2* X0 = a.X + b0 * a.ld_X;
+    float2* X1 = a.X + (live1 ? b1 : b0) * a.ld_X;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int j = (t + T * i + K / 2) & (K - 1);
+        X0[j] = lane_a(v[i]);
+        if (live1) X1[j] = lane_b(v[i]);
+    }
+}
+
 using ZoomKernel = void (*)(ZoomArgs);
+
+static ZoomKernel zoom_kernel2_for(int K) {
+    switch (K) {
+        case 16: return k_zoom2<16>;
+        case 32: return k_zoom2<32>;
+        case 64: return k_zoom2<64>;
+        case 128: return k_zoom2<128>;
+        case 256: return k_zoom2<256>;
+        case 512: return k_zoom2<512>;
+        case 1024: return k_zoom2<1024>;
+        case 2048: return k_zoom2<2048>;
+        case 4096: return k_zoom2<4096>;
+        case 8192: return k_zoom2<8192>;
+        default: return nullptr;
+    }
+}
 
 static ZoomKernel zoom_kernel_for(int K) {
     switch (K) {
@@ -168,6 +268,10 @@ bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, d
     }
     p->n = (int)n; p->d = (int)d; p->n_taps = (int)n_taps; p->K = (int)K; p->lout = (int)lout;
     p->rs = (int)rs;
+    // two-lane layout: taps (16 B) + polyphase pairs + float4 FFT area + offsets + slack
+    p->smem2 = (size_t)n_taps * 16 + (size_t)((d * rs + 1) / 2) * 16 + (size_t)padded_len((int)K) * 16 +
+               (size_t)n_taps * 4 + (size_t)kZoomGroup * T * 8;
+    p->dual = K >= 16 && K <= 8192 && p->smem2 <= 200 * 1024;
     p->Cn = cycles_to_fixed(0.5 * (f1 + f2) / fs);
     p->threads = T;
     p->smem = smem;
@@ -175,18 +279,22 @@ bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, d
 }
 
 cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
-                        const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st) {
+                        const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st,
+                        int lanes) {
     if (batch == 0) return cudaSuccess;
-    ZoomKernel k = zoom_kernel_for(p.K);
+    const bool dual = p.dual && batch >= 2 && lanes != 1;
+    ZoomKernel k = dual ? zoom_kernel2_for(p.K) : zoom_kernel_for(p.K);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    const size_t smem = dual ? p.smem2 : p.smem;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ZoomArgs a;
     a.x = x; a.batch = batch; a.n = p.n; a.ld_x = ld_x; a.taps = taps;
     a.n_taps = p.n_taps; a.d = p.d; a.logd = is_pow2(p.d) ? ilog2(p.d) : -1;
     a.lout = p.lout; a.rs = p.rs; a.Cn = p.Cn; a.tw = tw;
     a.X = X; a.ld_X = ld_X;
-    k<<<(unsigned)batch, p.threads, p.smem, st>>>(a);
+    const int64_t grid = dual ? (batch + 1) / 2 : batch;
+    k<<<(unsigned)grid, p.threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -70,6 +71,7 @@ struct spec_ctx {
     int device = 0;
     std::string err;
     float2* block_tw = nullptr;          // BlockFFT twiddles of every size
+    int lanes = 1;                       // 1: one FFT per thread group; 2: two packed lanes where possible
     std::vector<FftEntry> fft;
     std::vector<CztEntry> czt;
     uint64_t tick = 0;
@@ -233,6 +235,7 @@ spec_status spec_ctx_create(spec_ctx** ctx, int device) {
         return SPEC_ENOMEM;
     }
     c->device = device;
+    if (const char* ev = std::getenv("SPEC_LANES")) c->lanes = std::atoi(ev);
     {
         std::vector<float2> host((size_t)block_twiddle_total());
         block_twiddle_fill(host.data());
@@ -321,7 +324,7 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         }
     }
     cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ), tab,
-                               io.X, ld_X, st);
+                               io.X, ld_X, st, c->lanes);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
     return stage_out_finish(c, X, batch, bins, ld_X, st, io);
 }
@@ -385,7 +388,9 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
-    cudaError_t e = czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);
+    cudaError_t e = (czt_dual_ok(L) && c->lanes != 1)
+        ? czt_launch2(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st)
+        : czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
     return stage_out_finish(c, X, batch, m, ld_X, st, io);
 }
@@ -422,7 +427,7 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, K, ld_X, &io)) != SPEC_OK) return s;
     cudaError_t e = zoom_launch(p, io.x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), io.X,
-                                ld_X, st);
+                                ld_X, st, c->lanes);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
     return stage_out_finish(c, X, batch, K, ld_X, st, io);
 }

@@ -39,6 +39,7 @@ struct FftPlan {
     int Rc = 0;     // residues per CTA
     int E = 0, T = 0;   // elements per thread, threads per residue FFT
     int F = 0;      // traces per CTA (C == 1 only)
+    bool dual = false;  // two residues per thread (packed lanes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
     size_t smem = 0;
@@ -49,8 +50,11 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 // the host, rounded to float.
 int fft_table_entries(const FftPlan& p);
 void fft_fill_table(const FftPlan& p, float2* host);
+// lanes: 1 forces one FFT per thread group, otherwise the two-lane kernel is
+// used where the plan allows it.
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
-                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st);
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
+                       int lanes);
 
 // BlockFFT twiddle tables of every size 32 .. kMaxBlockFFT in one buffer.
 constexpr int kMaxBlockFFT = 16384;
@@ -71,6 +75,10 @@ bool czt_supported(int64_t n, int64_t m, std::string* why);
 cudaError_t czt_build_tables(const CztTables& t, const float2* tw, cudaStream_t st);
 cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
                        const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
+// Two traces per thread (packed lanes).
+bool czt_dual_ok(int L);
+cudaError_t czt_launch2(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
+                        const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
 
 // ---- Zoom FFT (k_zoom.cu) -------------------------------------------------
 struct ZoomPlan {
@@ -79,10 +87,13 @@ struct ZoomPlan {
     uint64_t Cn = 0; // frac(f_N / fs) in 2^-64 cycles
     int threads = 0;
     size_t smem = 0;
+    bool dual = false;   // two traces per CTA (packed lanes)
+    size_t smem2 = 0;
 };
 bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
                double f2, ZoomPlan* p, std::string* why);
 cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
-                        const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
+                        const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st,
+                        int lanes);
 
 }  // namespace spec

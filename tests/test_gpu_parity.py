@@ -80,6 +80,7 @@ CZT_CASES = [
     (3, 2048, 0.2e12, 2.5e12, 1024), (4, 1000, 0.1e12, 3.6e12, 256), (2, 1024, 0.8e12, 1.2e12, 512),
     (3, 2048, 2.5e12, 0.2e12, 1024), (2, 500, 1.0e12, 1.0e12, 1), (3, 8192, 0.3e12, 3.0e12, 4096),
     (2, 1, 0.5e12, 1.0e12, 1), (2, 3, 0.5e12, 1.0e12, 5), (5, 333, -2e12, 9.9e12, 77), (2, 64, 0.0, 19.6875e12, 64),
+    (1, 2048, 0.2e12, 2.5e12, 1024), (7, 4000, 0.3e12, 1.3e12, 4000),
 ]
 
 
@@ -108,6 +109,7 @@ ZOOM_CASES = [
     (3, 2048, 0.2e12, 2.5e12, 4, 63, 16384), (2, 2048, 1.0e12, 1.7e12, 1, 1, 4096),
     (3, 8192, 0.5e12, 1.5e12, 16, 127, 65536), (2, 8192, 0.5e12, 1.5e12, 4, 31, 65536),
     (4, 30, 0.5e12, 1.5e12, 2, 5, 64), (3, 1000, 0.1e12, 2.0e12, 8, 45, 8192), (2, 2047, 3e12, 4e12, 2, 64, 16384),
+    (1, 2048, 0.2e12, 2.5e12, 4, 63, 16384), (5, 3000, 0.2e12, 0.9e12, 3, 40, 24576),
 ]
 
 
