@@ -245,41 +245,78 @@ template <bool INV, class V> __device__ __forceinline__ void dft16(V* a) {
     t = a[11]; a[11] = a[14]; a[14] = t;
 }
 
+// cos(pi k/16), k = 0 .. 8
+__host__ __device__ constexpr float cos_pi16(int k) {
+    return k == 0 ? 1.0f : k == 1 ? 0.98078528040323044913f : k == 2 ? 0.92387953251128675613f
+         : k == 3 ? 0.83146961230254523708f : k == 4 ? 0.70710678118654752440f : k == 5 ? 0.55557023301960222474f
+         : k == 6 ? 0.38268343236508977173f : k == 7 ? 0.19509032201612826785f : 0.0f;
+}
+
+// 32 = 2 x 16: X[k] = E[k] + w32^k O[k], X[k + 16] = E[k] - w32^k O[k]
+template <bool INV, class V> __device__ __forceinline__ void dft32(V* a) {
+    V e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = a[2 * i];
+        o[i] = a[2 * i + 1];
+    }
+    dft16<INV>(e);
+    dft16<INV>(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        V t = o[k];
+        if (k == 8) t = rot90<INV>(t);
+        else if (k != 0) {
+            // w32^k = cos(pi k/16) -+ j sin(pi k/16), sin(pi k/16) = cos(pi (8-k)/16)
+            const float c = k < 8 ? cos_pi16(k) : -cos_pi16(16 - k);
+            const float s = k < 8 ? cos_pi16(8 - k) : cos_pi16(k - 8);
+            t = mulk(t, c, INV ? s : -s);
+        }
+        a[k] = vadd(e[k], t);
+        a[k + 16] = vsub(e[k], t);
+    }
+}
+
 template <int R, bool INV, class V> __device__ __forceinline__ void dft(V* a) {
     if constexpr (R == 2) dft2<INV>(a[0], a[1]);
     else if constexpr (R == 4) dft4<INV>(a[0], a[1], a[2], a[3]);
     else if constexpr (R == 8) dft8<INV>(a);
     else if constexpr (R == 16) dft16<INV>(a);
+    else if constexpr (R == 32) dft32<INV>(a);
 }
 
 // Padded shared-memory index: one spare slot per 16 keeps the stride-R writes
 // of the first Stockham pass free of bank conflicts.
 __host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+// Same with one spare slot per P (P = the radix of the first pass, whose
+// stride-P writes it spreads over the banks); padded_len(n) covers it.
+template <int P> __host__ __device__ constexpr int pidx_p(int i) { return i + i / P; }
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
 // ---------------------------------------------------------------- BlockFFT --
-// Radix plan of an LF-point FFT: radix-16 passes, then one pass of the
-// remaining factor (2, 4 or 8).  Pass p has NS = ns(p) (product of the
-// earlier radices) and span NS R.
-template <int LF> struct FFTShape {
-    static constexpr int E = LF < 16 ? LF : 16;
+// Radix plan of an LF-point FFT with EMAX (16 or 32) elements per thread:
+// radix-EMAX passes, then one pass of the remaining factor.  Pass p has
+// NS = ns(p) (product of the earlier radices) and span NS R.
+template <int LF, int EMAX = 16> struct FFTShape {
+    static constexpr int E = LF < EMAX ? LF : EMAX;
     static constexpr int T = LF / E;
     static constexpr int LOG = ilog2c(LF);
-    static constexpr int NP16 = LOG / 4;               // radix-16 passes
-    static constexpr int REM = 1 << (LOG % 4);         // trailing radix
-    static constexpr int NPASS = NP16 + (REM > 1 ? 1 : 0);
-    static constexpr int radix(int p) { return p < NP16 ? 16 : REM; }
+    static constexpr int LE = ilog2c(EMAX);
+    static constexpr int NPB = LOG / LE;               // full-radix passes
+    static constexpr int REM = 1 << (LOG % LE);        // trailing radix
+    static constexpr int NPASS = NPB + (REM > 1 ? 1 : 0);
+    static constexpr int radix(int p) { return p < NPB ? EMAX : REM; }
     static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
     // Twiddle table: pass p >= 1 holds w_{NS R}^{r k} at [off(p) + (r-1) NS + k],
     // r = 1 .. R-1, k < NS; (R-1) NS = ns(p+1) - ns(p), so off(p) = ns(p) - ns(1).
     static constexpr int tw_off(int p) { return ns(p) - ns(1); }
 };
 
-// Entries of the twiddle table of an LF-point BlockFFT: LF - 16 for LF > 16
-// (the first pass is radix-16 and needs none), 0 otherwise.
-__host__ __device__ constexpr int fft_twiddle_entries(int LF) { return LF > 16 ? LF - 16 : 0; }
+// Entries of the twiddle table of an LF-point BlockFFT: LF - EMAX for
+// LF > EMAX (the first pass needs none), 0 otherwise.
+__host__ __device__ constexpr int fft_twiddle_entries(int LF, int emax = 16) { return LF > emax ? LF - emax : 0; }
 
 // LF-point FFT by T = LF/E threads, on lane type V (float2: one FFT per
 // thread group; C2: two FFTs with the same twiddles, one per packed lane).
@@ -293,8 +330,8 @@ __host__ __device__ constexpr int fft_twiddle_entries(int LF) { return LF > 16 ?
 #endif
 constexpr int kTwChunk = SPEC_TW_CHUNK;   // twiddles loaded per compiler fence
 
-template <int LF, bool INV, class V = float2> struct BlockFFT {
-    using S = FFTShape<LF>;
+template <int LF, bool INV, class V = float2, int EMAX = 16> struct BlockFFT {
+    using S = FFTShape<LF, EMAX>;
     using TW = typename TwEntry<V>::type;
     using SM = typename SmemT<V>::type;
     static constexpr int E = S::E;
@@ -341,11 +378,11 @@ template <int LF, bool INV, class V = float2> struct BlockFFT {
             const int k = j & (NS - 1);
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) sts(s, pidx(base + r * NS), v[b + r * NB]);
+            for (int r = 0; r < R; ++r) sts(s, pidx_p<EMAX>(base + r * NS), v[b + r * NB]);
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = lds(s, pidx(t + T * i), (V*)nullptr);
+        for (int i = 0; i < E; ++i) v[i] = lds(s, pidx_p<EMAX>(t + T * i), (V*)nullptr);
     }
 
     template <int P>
@@ -362,10 +399,10 @@ template <int LF, bool INV, class V = float2> struct BlockFFT {
     }
 };
 
-// Fill the twiddle tables of every BlockFFT size 32 .. LMAX in float64; the
-// table of size LF starts at fft_twiddle_offset(LF).
-__host__ __device__ constexpr int fft_twiddle_offset(int LF) {
-    return LF <= 32 ? 0 : fft_twiddle_offset(LF >> 1) + fft_twiddle_entries(LF >> 1);
+// Offset of the table of size LF in a buffer holding the tables of every
+// size 2 EMAX .. LMAX (EMAX elements per thread) in increasing order.
+__host__ __device__ constexpr int fft_twiddle_offset(int LF, int emax = 16) {
+    return LF <= 2 * emax ? 0 : fft_twiddle_offset(LF >> 1, emax) + fft_twiddle_entries(LF >> 1, emax);
 }
 
 }  // namespace spec

@@ -17,6 +17,8 @@
 // generated once in float64.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+
 #include "fft_block.cuh"
 #include "spec_internal.h"
 
@@ -36,9 +38,9 @@ struct FftArgs {
     int64_t ld_X;
 };
 
-template <int LZ>
-__global__ void __launch_bounds__(512, 2) k_fft_real_padded(FftArgs a) {
-    using FFT = BlockFFT<LZ, false>;
+template <int LZ, int EMAX>
+__global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(FftArgs a) {
+    using FFT = BlockFFT<LZ, false, float2, EMAX>;
     constexpr int E = FFT::E;
     constexpr int T = FFT::T;
     extern __shared__ float2 smem[];
@@ -241,24 +243,45 @@ static FftKernel fft_kernel2_for(int LZ) {
     }
 }
 
-static FftKernel fft_kernel_for(int LZ) {
+static FftKernel fft_kernel_for(int LZ, int emax) {
+    if (emax == 32) {
+        switch (LZ) {
+            case 512: return k_fft_real_padded<512, 32>;
+            case 1024: return k_fft_real_padded<1024, 32>;
+            case 8192: return k_fft_real_padded<8192, 32>;
+            default: return nullptr;
+        }
+    }
     switch (LZ) {
-        case 1: return k_fft_real_padded<1>;
-        case 2: return k_fft_real_padded<2>;
-        case 4: return k_fft_real_padded<4>;
-        case 8: return k_fft_real_padded<8>;
-        case 16: return k_fft_real_padded<16>;
-        case 32: return k_fft_real_padded<32>;
-        case 64: return k_fft_real_padded<64>;
-        case 128: return k_fft_real_padded<128>;
-        case 256: return k_fft_real_padded<256>;
-        case 512: return k_fft_real_padded<512>;
-        case 1024: return k_fft_real_padded<1024>;
-        case 2048: return k_fft_real_padded<2048>;
-        case 4096: return k_fft_real_padded<4096>;
-        case 8192: return k_fft_real_padded<8192>;
+        case 1: return k_fft_real_padded<1, 16>;
+        case 2: return k_fft_real_padded<2, 16>;
+        case 4: return k_fft_real_padded<4, 16>;
+        case 8: return k_fft_real_padded<8, 16>;
+        case 16: return k_fft_real_padded<16, 16>;
+        case 32: return k_fft_real_padded<32, 16>;
+        case 64: return k_fft_real_padded<64, 16>;
+        case 128: return k_fft_real_padded<128, 16>;
+        case 256: return k_fft_real_padded<256, 16>;
+        case 512: return k_fft_real_padded<512, 16>;
+        case 1024: return k_fft_real_padded<1024, 16>;
+        case 2048: return k_fft_real_padded<2048, 16>;
+        case 4096: return k_fft_real_padded<4096, 16>;
+        case 8192: return k_fft_real_padded<8192, 16>;
         default: return nullptr;
     }
+}
+
+// Elements per thread of the residue FFTs.  Radix-32 passes save one
+// shared-memory exchange at 512, 1024 and 8192 points, but at 1024 points
+// (4096 traces x 2048 samples to 16384) they measured slower than radix 16
+// (150 vs 144 us: half the occupancy at 128 registers), so radix 16 is used;
+// the radix-32 kernels stay available through SPEC_FFT_EMAX=32.
+int fft_emax_for(int LF) {
+    static const int forced = [] {
+        const char* e = std::getenv("SPEC_FFT_EMAX");
+        return e ? std::atoi(e) : 16;
+    }();
+    return (forced == 32 && (LF == 512 || LF == 1024 || LF == 8192)) ? 32 : 16;
 }
 
 bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why) {
@@ -278,7 +301,8 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
         *why = "padded FFT: n_fft above 131072 needs the multi-pass path";
         return false;
     }
-    const int E = LZ < 16 ? (int)LZ : 16;
+    p->emax = fft_emax_for((int)LZ);
+    const int E = LZ < p->emax ? (int)LZ : p->emax;
     const int T = (int)LZ / E;
     p->H = (int)H;
     p->LZ = (int)LZ;
@@ -287,7 +311,7 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     p->Rc = (int)(R / C);
     p->E = E;
     p->T = T;
-    p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096;
+    p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096 && p->emax == 16;
     const int per_trace = p->dual ? (p->Rc / 2) * T : p->Rc * T;
     p->F = 1;
     if (C == 1) {
@@ -329,7 +353,7 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
         return cudaGetLastError();
     }
     const bool dual = p.dual && lanes != 1;
-    FftKernel k = dual ? fft_kernel2_for(p.LZ) : fft_kernel_for(p.LZ);
+    FftKernel k = dual ? fft_kernel2_for(p.LZ) : fft_kernel_for(p.LZ, p.emax);
     if (!k) return cudaErrorInvalidValue;
     FftArgs a;
     a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;

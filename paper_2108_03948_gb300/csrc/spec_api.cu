@@ -16,32 +16,44 @@
 
 namespace spec {
 
-int block_twiddle_total() { return fft_twiddle_offset(kMaxBlockFFT) + fft_twiddle_entries(kMaxBlockFFT); }
-int block_twiddle_offset(int LF) { return LF <= 16 ? 0 : fft_twiddle_offset(LF); }
+static int block_twiddle_total16() { return fft_twiddle_offset(kMaxBlockFFT) + fft_twiddle_entries(kMaxBlockFFT); }
+int block_twiddle_total() {
+    return block_twiddle_total16() + fft_twiddle_offset(kMaxBlockFFT, 32) + fft_twiddle_entries(kMaxBlockFFT, 32);
+}
+int block_twiddle_offset(int LF, int emax) {
+    if (emax == 32) return LF <= 32 ? 0 : block_twiddle_total16() + fft_twiddle_offset(LF, 32);
+    return LF <= 16 ? 0 : fft_twiddle_offset(LF);
+}
 
 // Twiddles of the Stockham passes of every BlockFFT size (the layout of
 // FFTShape::tw_off): pass p >= 1 of radix R after NS points holds
-// e^{-j 2 pi r k/(NS R)} at [NS - 16 + (r-1) NS + k].  float64, exact
+// e^{-j 2 pi r k/(NS R)} at [NS - EMAX + (r-1) NS + k].  float64, exact
 // argument reduction, rounded to float.
-void block_twiddle_fill(float2* host) {
+static void fill_emax(float2* host, int emax) {
     const double two_pi = 6.283185307179586476925286766559;
-    for (int LF = 32; LF <= kMaxBlockFFT; LF <<= 1) {
-        float2* o = host + fft_twiddle_offset(LF);
-        const int lg = ilog2(LF), np16 = lg / 4, rem = 1 << (lg % 4);
-        const int npass = np16 + (rem > 1 ? 1 : 0);
+    const int le = ilog2(emax);
+    for (int LF = 2 * emax; LF <= kMaxBlockFFT; LF <<= 1) {
+        float2* o = host + block_twiddle_offset(LF, emax);
+        const int lg = ilog2(LF), npb = lg / le, rem = 1 << (lg % le);
+        const int npass = npb + (rem > 1 ? 1 : 0);
         int ns = 1;
         for (int p = 0; p < npass; ++p) {
-            const int R = p < np16 ? 16 : rem;
+            const int R = p < npb ? emax : rem;
             if (p >= 1)
                 for (int r = 1; r < R; ++r)
                     for (int k = 0; k < ns; ++k) {
                         const int64_t S = (int64_t)ns * R;
                         const double ang = two_pi * (double)(((int64_t)r * k) % S) / (double)S;
-                        o[ns - 16 + (r - 1) * ns + k] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+                        o[ns - emax + (r - 1) * ns + k] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
                     }
             ns *= R;
         }
     }
+}
+
+void block_twiddle_fill(float2* host) {
+    fill_emax(host, 16);
+    fill_emax(host, 32);
 }
 
 uint64_t cycles_to_fixed(double cycles) {
@@ -323,7 +335,7 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
             tab = ne.tab;
         }
     }
-    cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ), tab,
+    cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ, p.emax), tab,
                                io.X, ld_X, st, c->lanes);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
     return stage_out_finish(c, X, batch, bins, ld_X, st, io);

@@ -40,6 +40,7 @@ struct FftPlan {
     int E = 0, T = 0;   // elements per thread, threads per residue FFT
     int F = 0;      // traces per CTA (C == 1 only)
     bool dual = false;  // two residues per thread (packed lanes)
+    int emax = 16;      // elements per thread (16 or 32: radix of the passes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
     size_t smem = 0;
@@ -56,11 +57,13 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
                        const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
                        int lanes);
 
-// BlockFFT twiddle tables of every size 32 .. kMaxBlockFFT in one buffer.
+// BlockFFT twiddle tables of every size up to kMaxBlockFFT in one buffer:
+// first the radix-16 layouts (sizes 32 ..), then the radix-32 ones (64 ..).
 constexpr int kMaxBlockFFT = 16384;
 int block_twiddle_total();
-int block_twiddle_offset(int LF);
+int block_twiddle_offset(int LF, int emax = 16);
 void block_twiddle_fill(float2* host);
+int fft_emax_for(int LF);
 
 // ---- chirp-z by Bluestein (k_czt.cu) --------------------------------------
 struct CztTables {
