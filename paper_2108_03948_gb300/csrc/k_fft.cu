@@ -220,6 +220,178 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     if (a.C > 1) cg::this_cluster().sync();
 }
 
+// ---------------------------------------------------------------------------
+// Pruned complex FFT with a rotated store: Y[(j + shift) mod K] = U[j],
+// U = FFT_K of u[0 .. nin-1] zero-padded to K.  The same residue
+// decomposition as above (R = K/LZ pre-twiddled LZ-point FFTs, a cluster of
+// C CTAs when K > 8192), but the input is complex and each CTA stores its
+// own contiguous chunk of U, so distributed shared memory is only written.
+// Used by the Zoom FFT when its K-point FFT does not fit one CTA (the
+// ascending-frequency order of Section 2.2 is the rotation by K/2).
+struct C2cArgs {
+    const float2* u;
+    int64_t ld_u;
+    int nin;
+    int64_t batch;
+    int K, logR, Rc, C, F, logChunk, trace_smem, shift;
+    const float2* tw;
+    const float2* tab;    // [w_K^{r t}: R x T][w_K^{r T i}: R x E]
+    float2* X;
+    int64_t ld_X;
+};
+
+template <int LZ>
+__global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
+    using FFT = BlockFFT<LZ, false>;
+    constexpr int E = FFT::E;
+    constexpr int T = FFT::T;
+    extern __shared__ float2 smem[];
+
+    const int per_trace = a.Rc * T;
+    const int tid = threadIdx.x;
+    const int f = tid / per_trace;
+    const int lt = tid - f * per_trace;
+    const int rl = lt / T;
+    const int t = lt - rl * T;
+    const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
+    const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
+    const bool live = b < a.batch;
+    const int R = 1 << a.logR;
+    const int r = rank * a.Rc + rl;
+    float2* zs = smem + f * a.trace_smem;
+    float2* s = zs + rl * padded_len(LZ);
+
+    float2 v[E];
+    {
+        const float2 wt = __ldg(a.tab + r * T + t);
+        const float2* wi = a.tab + R * T + r * E;
+        const float2* ur = a.u + (live ? b : 0) * a.ld_u;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            const float2 z = (live && m < a.nin) ? __ldg(ur + m) : make_float2(0.f, 0.f);
+            v[i] = cmul(z, cmul(wt, __ldg(wi + i)));
+        }
+    }
+    FFT::run(v, s, t, a.tw);
+
+    const int chunk = 1 << a.logChunk;
+    __syncthreads();
+    if (a.C == 1) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
+        __syncthreads();
+    } else {
+        cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int k = ((t + T * i) << a.logR) + r;
+            cl.map_shared_rank(zs, k >> a.logChunk)[pidx(k & (chunk - 1))] = v[i];
+        }
+        cl.sync();
+    }
+    if (live) {
+        float2* Xr = a.X + b * a.ld_X;
+        const int j0 = rank * chunk;
+        for (int j = lt; j < chunk; j += per_trace) Xr[(j0 + j + a.shift) & (a.K - 1)] = zs[pidx(j)];
+    }
+}
+
+using C2cKernel = void (*)(C2cArgs);
+
+static C2cKernel c2c_kernel_for(int LZ) {
+    switch (LZ) {
+        case 16: return k_fft_c2c_pruned<16>;
+        case 32: return k_fft_c2c_pruned<32>;
+        case 64: return k_fft_c2c_pruned<64>;
+        case 128: return k_fft_c2c_pruned<128>;
+        case 256: return k_fft_c2c_pruned<256>;
+        case 512: return k_fft_c2c_pruned<512>;
+        case 1024: return k_fft_c2c_pruned<1024>;
+        case 2048: return k_fft_c2c_pruned<2048>;
+        case 4096: return k_fft_c2c_pruned<4096>;
+        case 8192: return k_fft_c2c_pruned<8192>;
+        default: return nullptr;
+    }
+}
+
+bool c2c_plan(int64_t batch, int64_t nin, int64_t K, FftPlan* p, std::string* why) {
+    *p = FftPlan();
+    int64_t LZ = std::max<int64_t>(16, next_pow2(nin));
+    LZ = std::min<int64_t>(LZ, K);
+    if (K < 16 || LZ > kTile) {
+        *why = "pruned FFT: needs 16 <= K and at most 8192 nonzero inputs";
+        return false;
+    }
+    const int64_t R = K / LZ;
+    const int64_t C = std::max<int64_t>(1, K / kTile);
+    if (C > 8) {
+        *why = "pruned FFT: K above 65536 needs the multi-pass path";
+        return false;
+    }
+    p->H = (int)K;
+    p->LZ = (int)LZ;
+    p->R = (int)R;
+    p->C = (int)C;
+    p->Rc = (int)(R / C);
+    p->E = 16;
+    p->T = (int)LZ / 16;
+    const int per_trace = p->Rc * p->T;
+    p->F = 1;
+    if (C == 1) p->F = (int)std::min<int64_t>(std::max(1, 256 / per_trace), std::max<int64_t>(1, batch));
+    p->trace_smem = std::max(p->Rc * padded_len((int)LZ), padded_len((int)(K / C)));
+    p->threads = p->F * per_trace;
+    p->smem = (size_t)p->F * p->trace_smem * sizeof(float2);
+    return true;
+}
+
+int c2c_table_entries(const FftPlan& p) { return p.R * p.T + p.R * p.E; }
+
+void c2c_fill_table(const FftPlan& p, float2* host) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const int64_t K = p.H;
+    auto w = [&](int64_t num) {
+        const double ang = two_pi * (double)(num % K) / (double)K;
+        return make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    };
+    float2* o = host;
+    for (int r = 0; r < p.R; ++r)
+        for (int t = 0; t < p.T; ++t) *o++ = w((int64_t)r * t);
+    for (int r = 0; r < p.R; ++r)
+        for (int i = 0; i < p.E; ++i) *o++ = w((int64_t)r * p.T * i);
+}
+
+cudaError_t c2c_launch(const FftPlan& p, const float2* u, int64_t ld_u, int nin, int64_t batch, int shift,
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    C2cKernel k = c2c_kernel_for(p.LZ);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    C2cArgs a;
+    a.u = u; a.ld_u = ld_u; a.nin = nin; a.batch = batch;
+    a.K = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = p.F;
+    a.logChunk = ilog2(p.H / p.C); a.trace_smem = p.trace_smem; a.shift = shift;
+    a.tw = tw; a.tab = tab; a.X = X; a.ld_X = ld_X;
+    const int64_t groups = (batch + p.F - 1) / p.F;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(groups * p.C));
+    cfg.blockDim = dim3(p.threads);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    if (p.C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = p.C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 // n_fft == 1: the single bin is x[0].
 __global__ void k_fft_len1(const float* x, int64_t batch, int64_t ld_x, float2* X, int64_t ld_X) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

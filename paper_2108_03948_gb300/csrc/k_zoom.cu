@@ -203,6 +203,110 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom2(ZoomArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Large Zoom FFTs (a long trace, or N_FFT/D above one CTA): the FIR-decimate
+// step runs here, kFirChunk kept outputs per CTA and many CTAs per trace, and
+// writes u[m] (mix and rotation applied) to a workspace; the K-point FFT and
+// the ascending-frequency store follow in the pruned cluster FFT
+// (k_fft_c2c_pruned).  Same arithmetic as k_zoom.
+constexpr int kFirChunk = 256;
+
+struct FirArgs {
+    const float* x;
+    int64_t batch;
+    int n;
+    int64_t ld_x;
+    const float* taps;
+    int n_taps, d, logd, lout, rs, chunks;
+    uint64_t Cn;
+    float2* u;
+    int64_t ld_u;
+};
+
+__global__ void __launch_bounds__(kFirChunk) k_zoom_fir(FirArgs a) {
+    extern __shared__ float4 smem4[];
+    const int t = threadIdx.x;
+    const int64_t b = blockIdx.x / a.chunks;
+    const int m0 = (int)(blockIdx.x % a.chunks) * kFirChunk;
+    const int J = a.n_taps - 1;
+    const int D = a.d;
+    float4* tap = smem4;
+    float* xs = reinterpret_cast<float*>(smem4 + a.n_taps);
+
+    for (int k = t; k < a.n_taps; k += kFirChunk) {
+        const float h = __ldg(a.taps + k);
+        const float2 e = unit_fixed(a.Cn * (uint64_t)k, false);
+        const int q = J - k;
+        tap[k] = make_float4(h * e.x, h * e.y, __int_as_float((q % D) * a.rs + q / D), 0.f);
+    }
+    // window of the extended trace for outputs m0 .. m0 + kFirChunk - 1:
+    // local index jj = j - m0 D, sample x[j - J]
+    const float* xr = a.x + b * a.ld_x;
+    const int total = D * a.rs;
+    const int64_t base = (int64_t)m0 * D - J;
+    for (int jj = t; jj < total; jj += kFirChunk) {
+        const int64_t src = base + jj;
+        const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
+        const int slot = a.logd >= 0 ? (jj & (D - 1)) * a.rs + (jj >> a.logd) : (jj % D) * a.rs + jj / D;
+        xs[slot] = xv;
+    }
+    __syncthreads();
+    const int m = m0 + t;
+    if (m < a.lout) {
+        float re = 0.f, im = 0.f;
+        const float* xm = xs + t;
+        for (int k = 0; k < a.n_taps; ++k) {
+            const float4 g = tap[k];
+            const float xv = xm[__float_as_int(g.z)];
+            re = fmaf(g.x, xv, re);
+            im = fmaf(g.y, xv, im);
+        }
+        const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
+        a.u[b * a.ld_u + m] = cmul(make_float2(re, im), rot);
+    }
+}
+
+bool zoom_big_plan(int64_t batch, int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
+                   double f2, ZoomPlan* p, std::string* why) {
+    *p = ZoomPlan();
+    const int64_t K = n_fft / d;
+    const int64_t lout = (n + n_taps - 1 + d - 1) / d;
+    int64_t rs = kFirChunk + (n_taps - 1) / d + 2;
+    if ((rs & 1) == 0) ++rs;
+    const size_t smem = (size_t)n_taps * 16 + (size_t)d * rs * 4;
+    if (smem > 200 * 1024) {
+        *why = "zoom: taps and decimation too large for the FIR tile";
+        return false;
+    }
+    FftPlan fp;
+    if (!c2c_plan(batch, lout, K, &fp, why)) return false;
+    p->n = (int)n; p->d = (int)d; p->n_taps = (int)n_taps; p->K = (int)K; p->lout = (int)lout;
+    p->rs = (int)rs;
+    p->Cn = cycles_to_fixed(0.5 * (f1 + f2) / fs);
+    p->threads = kFirChunk;
+    p->smem = smem;
+    p->big = true;
+    p->fft = fp;
+    return true;
+}
+
+cudaError_t zoom_big_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x, const float* taps,
+                            float2* work, const float2* tw, const float2* tab, float2* X, int64_t ld_X,
+                            cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    FirArgs a;
+    a.x = x; a.batch = batch; a.n = p.n; a.ld_x = ld_x; a.taps = taps;
+    a.n_taps = p.n_taps; a.d = p.d; a.logd = is_pow2(p.d) ? ilog2(p.d) : -1; a.lout = p.lout; a.rs = p.rs;
+    a.chunks = (p.lout + kFirChunk - 1) / kFirChunk; a.Cn = p.Cn;
+    a.u = work; a.ld_u = p.fft.LZ;
+    cudaError_t e = cudaFuncSetAttribute(k_zoom_fir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    k_zoom_fir<<<(unsigned)(batch * a.chunks), kFirChunk, p.smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return c2c_launch(p.fft, work, p.fft.LZ, p.lout, batch, p.K / 2, tw, tab, X, ld_X, st);
+}
+
 using ZoomKernel = void (*)(ZoomArgs);
 
 static ZoomKernel zoom_kernel2_for(int K) {

@@ -75,6 +75,7 @@ struct CztEntry {
 };
 
 struct FftEntry {
+    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables
     int H = 0, LZ = 0;
     float2* tab = nullptr;
 };
@@ -87,8 +88,8 @@ struct spec_ctx {
     std::vector<FftEntry> fft;
     std::vector<CztEntry> czt;
     uint64_t tick = 0;
-    void* stage[3] = {nullptr, nullptr, nullptr};   // x, X, taps
-    size_t stage_bytes[3] = {0, 0, 0};
+    void* stage[4] = {nullptr, nullptr, nullptr, nullptr};   // x, X, taps, workspace
+    size_t stage_bytes[4] = {0, 0, 0, 0};
 };
 
 static std::string g_create_err;
@@ -213,6 +214,32 @@ spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, 
     return SPEC_OK;
 }
 
+// Per-shape twiddle tables of the padded real FFT (kind 0) and of the pruned
+// complex FFT (kind 1), built on the host in float64 and cached.
+spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab) {
+    for (auto& it : c->fft)
+        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ) {
+            *tab = it.tab;
+            return SPEC_OK;
+        }
+    FftEntry ne;
+    ne.kind = kind;
+    ne.H = p.H;
+    ne.LZ = p.LZ;
+    std::vector<float2> host((size_t)(kind == 0 ? fft_table_entries(p) : c2c_table_entries(p)));
+    if (kind == 0) fft_fill_table(p, host.data());
+    else c2c_fill_table(p, host.data());
+    cudaError_t e = cudaMalloc(&ne.tab, host.size() * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(ne.tab, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (ne.tab) cudaFree(ne.tab);
+        return cuda_fail(c, e, "FFT tables");
+    }
+    c->fft.push_back(ne);
+    *tab = ne.tab;
+    return SPEC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -278,7 +305,7 @@ void spec_ctx_destroy(spec_ctx* c) {
         for (auto& en : c->fft)
             if (en.tab) cudaFree(en.tab);
         if (c->block_tw) cudaFree(c->block_tw);
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 4; ++i)
             if (c->stage[i]) cudaFree(c->stage[i]);
         cudaGetLastError();
     }
@@ -315,26 +342,7 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, bins, ld_X, &io)) != SPEC_OK) return s;
     const float2* tab = nullptr;
-    if (p.H > 0) {
-        for (auto& it : c->fft)
-            if (it.H == p.H && it.LZ == p.LZ) tab = it.tab;
-        if (!tab) {
-            FftEntry ne;
-            ne.H = p.H;
-            ne.LZ = p.LZ;
-            std::vector<float2> host((size_t)fft_table_entries(p));
-            fft_fill_table(p, host.data());
-            cudaError_t e = cudaMalloc(&ne.tab, host.size() * sizeof(float2));
-            if (e == cudaSuccess)
-                e = cudaMemcpy(ne.tab, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) {
-                if (ne.tab) cudaFree(ne.tab);
-                return cuda_fail(c, e, "FFT tables");
-            }
-            c->fft.push_back(ne);
-            tab = ne.tab;
-        }
-    }
+    if (p.H > 0 && (s = plan_table(c, 0, p, &tab)) != SPEC_OK) return s;
     cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ, p.emax), tab,
                                io.X, ld_X, st, c->lanes);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
@@ -424,7 +432,11 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
         return fail(c, SPEC_EINVAL, "ceil((n + n_taps - 1)/d) must not exceed n_fft/d");
     ZoomPlan p;
     std::string why;
-    if (!zoom_plan(n, d, n_taps, n_fft, fs, f1, f2, &p, &why)) return fail(c, SPEC_EUNSUPPORTED, why);
+    if (!zoom_plan(n, d, n_taps, n_fft, fs, f1, f2, &p, &why)) {
+        std::string why2;
+        if (!zoom_big_plan(batch, n, d, n_taps, n_fft, fs, f1, f2, &p, &why2))
+            return fail(c, SPEC_EUNSUPPORTED, why + "; " + why2);
+    }
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -438,8 +450,17 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, K, ld_X, &io)) != SPEC_OK) return s;
-    cudaError_t e = zoom_launch(p, io.x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), io.X,
-                                ld_X, st, c->lanes);
+    cudaError_t e;
+    if (p.big) {
+        const float2* tab = nullptr;
+        if ((s = plan_table(c, 1, p.fft, &tab)) != SPEC_OK) return s;
+        if ((s = ensure_stage(c, 3, (size_t)batch * p.fft.LZ * sizeof(float2))) != SPEC_OK) return s;
+        e = zoom_big_launch(p, io.x, batch, ld_x, taps_d, (float2*)c->stage[3],
+                            c->block_tw + block_twiddle_offset(p.fft.LZ), tab, io.X, ld_X, st);
+    } else {
+        e = zoom_launch(p, io.x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), io.X, ld_X, st,
+                        c->lanes);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
     return stage_out_finish(c, X, batch, K, ld_X, st, io);
 }

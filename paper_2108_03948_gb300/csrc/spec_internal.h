@@ -57,6 +57,14 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
                        const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
                        int lanes);
 
+// Pruned complex FFT with rotated store (k_fft.cu), planned in an FftPlan
+// with H = K: Y[(j + shift) mod K] = FFT_K(u zero-padded)[j].
+bool c2c_plan(int64_t batch, int64_t nin, int64_t K, FftPlan* p, std::string* why);
+int c2c_table_entries(const FftPlan& p);
+void c2c_fill_table(const FftPlan& p, float2* host);
+cudaError_t c2c_launch(const FftPlan& p, const float2* u, int64_t ld_u, int nin, int64_t batch, int shift,
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st);
+
 // BlockFFT twiddle tables of every size up to kMaxBlockFFT in one buffer:
 // first the radix-16 layouts (sizes 32 ..), then the radix-32 ones (64 ..).
 constexpr int kMaxBlockFFT = 16384;
@@ -92,9 +100,18 @@ struct ZoomPlan {
     size_t smem = 0;
     bool dual = false;   // two traces per CTA (packed lanes)
     size_t smem2 = 0;
+    bool big = false;    // FIR kernel + pruned cluster FFT (zoom_big_*)
+    FftPlan fft;         // the K-point FFT of the big path
 };
 bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
                double f2, ZoomPlan* p, std::string* why);
+// Large Zoom FFTs: FIR-decimate into `work` ([batch][fft.LZ] float2), then
+// the pruned cluster FFT.
+bool zoom_big_plan(int64_t batch, int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, double f1,
+                   double f2, ZoomPlan* p, std::string* why);
+cudaError_t zoom_big_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x, const float* taps,
+                            float2* work, const float2* tw, const float2* tab, float2* X, int64_t ld_X,
+                            cudaStream_t st);
 cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
                         const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st,
                         int lanes);
