@@ -167,6 +167,45 @@ SPEC_API spec_status spec_czt_static(const float* x, int64_t batch, int64_t n, i
                                      double fs, double f1, double f2, int64_t m,
                                      float* X, int64_t ld_X, void* stream);
 
+/*
+ * Ragged batches: many traces, each with its own length, band, point count,
+ * decimation and taps, in one call.  Each descriptor is one independent
+ * spec_fft / spec_czt / spec_zoom problem on one trace (the paper's three
+ * transforms, Sections 2.1-2.3, with the conventions documented above):
+ *   trace   x_pool[x_off .. x_off + n)
+ *   output  X_pool + out_off (complex elements): n_fft/2 + 1 bins (FFT),
+ *           m bins (CZT) or n_fft/d bins (Zoom), in the orders above
+ *   kind    SPEC_KIND_FFT uses n, n_fft; SPEC_KIND_CZT uses n, f1, f2, m;
+ *           SPEC_KIND_ZOOM uses n, f1, f2, d, n_fft and the taps
+ *           taps_pool[taps_off .. taps_off + n_taps).
+ * fs is shared by the batch.  The pools are device pointers; the descriptor
+ * array is host memory and is copied.  Outputs of different descriptors
+ * must not overlap (not checked).
+ * The first call with a descriptor list synchronises `stream`, builds a plan
+ * (per-trace tables, class grouping, variant autotuning by timing, one CUDA
+ * graph with a launch per class) and caches it in the context; a repeated
+ * call with identical descriptors and pools is one graph launch,
+ * asynchronous on `stream`.  Every descriptor is validated before anything
+ * runs (SPEC_EINVAL / SPEC_EUNSUPPORTED with the descriptor's index in
+ * spec_last_error).
+ */
+typedef enum { SPEC_KIND_FFT = 0, SPEC_KIND_CZT = 1, SPEC_KIND_ZOOM = 2 } spec_kind;
+
+typedef struct {
+    int64_t x_off;      /* first sample in x_pool (floats)              */
+    int64_t n;          /* samples                                      */
+    int64_t out_off;    /* first bin in X_pool (complex elements)       */
+    double f1, f2;      /* band (CZT, Zoom)                             */
+    int64_t n_fft;      /* padded length (FFT, Zoom)                    */
+    int64_t m;          /* CZT points                                   */
+    int64_t d;          /* Zoom decimation                              */
+    int64_t taps_off;   /* first tap in taps_pool (Zoom)                */
+    int64_t n_taps;     /* taps (Zoom)                                  */
+} spec_desc;
+
+SPEC_API spec_status spec_ragged(spec_ctx* ctx, int kind, const spec_desc* descs, int64_t count, double fs,
+                                 const float* x_pool, const float* taps_pool, float* X_pool, void* stream);
+
 /* ---- host-only helpers (pure functions, no CUDA calls) ----------------- */
 
 /* Zeros to append to an N_FFT-sample record so that its bin spacing shrinks

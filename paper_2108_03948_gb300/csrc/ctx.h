@@ -1,0 +1,49 @@
+// ctx.h -- the library context (opaque to callers of include/spec.h) and the
+// helpers the API translation units share.  Internal.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "spec.h"
+#include "spec_internal.h"
+
+struct CztEntry {
+    spec::CztTables t;
+    void* mem = nullptr;
+    cudaEvent_t ready = nullptr;
+    uint64_t last_use = 0;
+};
+
+struct FftEntry {
+    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables
+    int H = 0, LZ = 0, emax = 16;
+    float2* tab = nullptr;
+};
+
+struct RaggedPlan;       // ragged.cu
+void ragged_plan_free(RaggedPlan* p);
+
+struct spec_ctx {
+    int device = 0;
+    std::string err;
+    float2* block_tw = nullptr;          // BlockFFT twiddles of every size
+    int lanes = 1;                       // 1: one FFT per thread group; 2: two packed lanes where possible
+    std::vector<FftEntry> fft;
+    std::vector<CztEntry> czt;
+    std::vector<RaggedPlan*> ragged;     // cached ragged-batch plans (graph + per-trace tables)
+    uint64_t tick = 0;
+    void* stage[4] = {nullptr, nullptr, nullptr, nullptr};   // x, X, taps, workspace
+    size_t stage_bytes[4] = {0, 0, 0, 0};
+};
+
+namespace spec {
+spec_status ctx_fail(spec_ctx* c, spec_status s, const std::string& why);
+spec_status ctx_cuda_fail(spec_ctx* c, cudaError_t e, const char* what);
+bool ctx_is_device_ptr(const void* p);
+// Cached per-shape twiddle tables: kind 0 padded real FFT, kind 1 pruned complex FFT.
+spec_status ctx_plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab);
+}  // namespace spec

@@ -294,6 +294,7 @@ __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 template <int P> __host__ __device__ constexpr int pidx_p(int i) { return i + i / P; }
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+__host__ __device__ constexpr bool is_pow2_dev(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // ---------------------------------------------------------------- BlockFFT --
 // Radix plan of an LF-point FFT with EMAX (16 or 32) elements per thread:

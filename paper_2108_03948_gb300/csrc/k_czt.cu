@@ -73,6 +73,8 @@ struct BluesteinArgs {
     int64_t ld_X;
     int F;
     const float2* tw;
+    const RaggedItem* items;   // ragged batch: per-trace placement, n, m, tables (else null)
+    const float2* tables;      // ragged batch: per-trace tables pre | V | post at items[b].tab_off
 };
 
 template <int L>
@@ -86,25 +88,38 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, F
     const int64_t b = (int64_t)blockIdx.x * a.F + f;
     const bool live = b < a.batch;
     float2* s = smem + f * padded_len(L);
-    const float* xr = a.x + (live ? b : 0) * a.ld_x;
+    int n = a.n, m = a.m;
+    const float2 *pre = a.pre, *V = a.V, *post = a.post;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+        m = it.m;
+        pre = a.tables + it.tab_off;
+        V = pre + n;
+        post = V + L;
+    }
+    const float* xr = a.x + xo;
 
     float2 v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int nn = t + T * i;
-        v[i] = (live && nn < a.n) ? cscale(__ldg(&a.pre[nn]), __ldg(xr + nn)) : make_float2(0.f, 0.f);
+        v[i] = (live && nn < n) ? cscale(__ldg(&pre[nn]), __ldg(xr + nn)) : make_float2(0.f, 0.f);
     }
     Fw::run(v, s, t, a.tw);
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(&a.V[t + T * i]));
+    for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(&V[t + T * i]));
     int ti = t;                        // opaque copy: see k_czt_bluestein2
     asm volatile("" : "+r"(ti));
     Iv::run(v, s, ti, a.tw);
-    float2* Xr = a.X + (live ? b : 0) * a.ld_X;
+    float2* Xr = a.X + Xo;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int k = t + T * i;
-        if (live && k < a.m) Xr[k] = cmul(v[i], __ldg(&a.post[k]));
+        if (live && k < m) Xr[k] = cmul(v[i], __ldg(&post[k]));
     }
 }
 
@@ -217,7 +232,7 @@ cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_
     const size_t smem = (size_t)F * padded_len(t.L) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    BluesteinArgs a;
+    BluesteinArgs a = {};
     a.x = x; a.batch = batch; a.n = t.n; a.ld_x = ld_x; a.m = t.m;
     a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F; a.tw = tw;
     const int64_t grid = (batch + F - 1) / F;
@@ -256,6 +271,96 @@ cudaError_t czt_launch2(const CztTables& t, const float* x, int64_t batch, int64
     a.tw = tw;
     const int64_t grid = (pairs + F - 1) / F;
     bk<<<(unsigned)grid, F * T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches: every trace has its own (N, M, band), so its tables
+// pre | V | post live at items[b].tab_off of one buffer; built once per plan.
+__global__ void k_czt_pre_post_ragged(const RaggedItem* items, float2* tables, int L) {
+    const RaggedItem it = items[blockIdx.x];
+    float2* pre = tables + it.tab_off;
+    float2* post = pre + it.n + L;
+    const int cnt = max(it.n, it.m);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint64_t ii = (uint64_t)i;
+        if (i < it.n) pre[i] = unit_fixed_f64(it.A * ii + it.B * (ii * ii), true);
+        if (i < it.m) post[i] = unit_fixed_f64(it.B * (ii * ii), true);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(FFTShape<L>::T) k_czt_kernel_spectrum_ragged(const RaggedItem* items, float2* tables,
+                                                                              const float2* tw) {
+    using FFT = BlockFFT<L, false>;
+    constexpr int E = FFT::E, T = FFT::T;
+    extern __shared__ float2 smem[];
+    const RaggedItem it = items[blockIdx.x];
+    const int t = threadIdx.x;
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int idx = t + T * i;
+        int64_t mm;
+        bool nz = true;
+        if (idx < it.m) mm = idx;
+        else if (idx >= L - it.n + 1) mm = (int64_t)idx - L;
+        else { nz = false; mm = 0; }
+        v[i] = nz ? unit_fixed_f64(it.B * (uint64_t)(mm * mm), false) : make_float2(0.f, 0.f);
+    }
+    FFT::run(v, smem, t, tw);
+    float2* V = tables + it.tab_off + it.n;
+    const float inv = 1.0f / (float)L;
+#pragma unroll
+    for (int i = 0; i < E; ++i) V[t + T * i] = cscale(v[i], inv);
+}
+
+using VRagged = void (*)(const RaggedItem*, float2*, const float2*);
+
+template <int L> static void pickr(int want, BsKernel* bk, VRagged* vk) {
+    if (want == L) { *bk = k_czt_bluestein<L>; *vk = k_czt_kernel_spectrum_ragged<L>; }
+}
+
+static bool ragged_kernels_for(int L, BsKernel* bk, VRagged* vk) {
+    *bk = nullptr; *vk = nullptr;
+    pickr<16>(L, bk, vk); pickr<32>(L, bk, vk); pickr<64>(L, bk, vk); pickr<128>(L, bk, vk);
+    pickr<256>(L, bk, vk); pickr<512>(L, bk, vk); pickr<1024>(L, bk, vk); pickr<2048>(L, bk, vk);
+    pickr<4096>(L, bk, vk); pickr<8192>(L, bk, vk); pickr<16384>(L, bk, vk);
+    return *bk != nullptr;
+}
+
+cudaError_t czt_ragged_tables(int L, const RaggedItem* items, int64_t count, float2* tables, const float2* tw,
+                              cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    BsKernel bk;
+    VRagged vk;
+    if (!ragged_kernels_for(L, &bk, &vk)) return cudaErrorInvalidValue;
+    k_czt_pre_post_ragged<<<(unsigned)count, 256, 0, st>>>(items, tables, L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)padded_len(L) * sizeof(float2);
+    e = cudaFuncSetAttribute(vk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    vk<<<(unsigned)count, L / 16, smem, st>>>(items, tables, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t czt_ragged_launch(int L, const RaggedItem* items, int64_t count, const float* x_pool,
+                              const float2* tables, const float2* tw, float2* X_pool, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    BsKernel bk;
+    VRagged vk;
+    if (!ragged_kernels_for(L, &bk, &vk)) return cudaErrorInvalidValue;
+    const int T = L / 16;
+    int F = std::max(1, 256 / T);
+    F = (int)std::min<int64_t>(F, count);
+    const size_t smem = (size_t)F * padded_len(L) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    BluesteinArgs a = {};
+    a.x = x_pool; a.batch = count; a.X = X_pool; a.F = F; a.tw = tw;
+    a.items = items; a.tables = tables;
+    bk<<<(unsigned)((count + F - 1) / F), F * T, smem, st>>>(a);
     return cudaGetLastError();
 }
 

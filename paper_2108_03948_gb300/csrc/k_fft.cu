@@ -36,6 +36,7 @@ struct FftArgs {
     const float2* tab;    // [w_H^{r t}: R x T][w_H^{r T i}: R x E][w_{2H}^k: H/2 + 1]
     float2* X;
     int64_t ld_X;
+    const RaggedItem* items;   // ragged batch: per-trace x / X offsets and n (else null)
 };
 
 template <int LZ, int EMAX>
@@ -54,6 +55,14 @@ __global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(F
     const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
     const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
     const bool live = b < a.batch;
+    int n = a.n;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+    }
     const int R = 1 << a.logR;
     const int r = rank * a.Rc + rl;              // residue of this thread's FFT
     const int H = a.H;
@@ -65,13 +74,13 @@ __global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(F
     {
         const float2 wt = __ldg(a.tab + r * T + t);
         const float2* wi = a.tab + R * T + r * E;
-        const float* xr = a.x + (live ? b : 0) * a.ld_x;
+        const float* xr = a.x + xo;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int m = t + T * i;
             float re = 0.f, im = 0.f;
-            if (live && 2 * m < a.n) re = __ldg(xr + 2 * m);
-            if (live && 2 * m + 1 < a.n) im = __ldg(xr + 2 * m + 1);
+            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
             v[i] = cmul(make_float2(re, im), cmul(wt, __ldg(wi + i)));
         }
     }
@@ -101,7 +110,7 @@ __global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(F
     const int per_cta = (pairs + a.C - 1) / a.C;
     const int k0 = rank * per_cta;
     const int k1 = min(pairs, k0 + per_cta);
-    float2* Xr = a.X + (live ? b : 0) * a.ld_X;
+    float2* Xr = a.X + Xo;
     const float2* wp = a.tab + R * T + R * E;
     for (int k = k0 + lt; k < k1 && live; k += per_trace) {
         const int kb = (H - k) & (H - 1);
@@ -146,6 +155,14 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
     const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
     const bool live = b < a.batch;
+    int n = a.n;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+    }
     const int R = 1 << a.logR;
     const int ra = rank * a.Rc + gl;             // lane a residue
     const int rb = ra + G;                       // lane b residue
@@ -158,13 +175,13 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
         const float2 wta = __ldg(a.tab + ra * T + t), wtb = __ldg(a.tab + rb * T + t);
         const float2* wia = a.tab + R * T + ra * E;
         const float2* wib = a.tab + R * T + rb * E;
-        const float* xr = a.x + (live ? b : 0) * a.ld_x;
+        const float* xr = a.x + xo;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int m = t + T * i;
             float re = 0.f, im = 0.f;
-            if (live && 2 * m < a.n) re = __ldg(xr + 2 * m);
-            if (live && 2 * m + 1 < a.n) im = __ldg(xr + 2 * m + 1);
+            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
             const float2 z = make_float2(re, im);
             v[i] = c2(cmul(z, cmul(wta, __ldg(wia + i))), cmul(z, cmul(wtb, __ldg(wib + i))));
         }
@@ -197,7 +214,7 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     const int per_cta = (pairs + a.C - 1) / a.C;
     const int k0 = rank * per_cta;
     const int k1 = min(pairs, k0 + per_cta);
-    float2* Xr = a.X + (live ? b : 0) * a.ld_X;
+    float2* Xr = a.X + Xo;
     const float2* wp = a.tab + R * T + R * E;
     for (int k = k0 + lt; k < k1 && live; k += per_trace) {
         const int kb = (H - k) & (H - 1);
@@ -238,6 +255,7 @@ struct C2cArgs {
     const float2* tab;    // [w_K^{r t}: R x T][w_K^{r T i}: R x E]
     float2* X;
     int64_t ld_X;
+    const RaggedItem* items;   // ragged batch: nin = lout, u / X offsets (else null)
 };
 
 template <int LZ>
@@ -256,6 +274,14 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
     const int rank = a.C > 1 ? (int)(blockIdx.x % a.C) : 0;
     const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
     const bool live = b < a.batch;
+    int nin = a.nin;
+    int64_t uo = (live ? b : 0) * a.ld_u, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        uo = it.u_off;
+        Xo = it.out_off;
+        nin = it.lout;
+    }
     const int R = 1 << a.logR;
     const int r = rank * a.Rc + rl;
     float2* zs = smem + f * a.trace_smem;
@@ -265,11 +291,11 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
     {
         const float2 wt = __ldg(a.tab + r * T + t);
         const float2* wi = a.tab + R * T + r * E;
-        const float2* ur = a.u + (live ? b : 0) * a.ld_u;
+        const float2* ur = a.u + uo;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int m = t + T * i;
-            const float2 z = (live && m < a.nin) ? __ldg(ur + m) : make_float2(0.f, 0.f);
+            const float2 z = (live && m < nin) ? __ldg(ur + m) : make_float2(0.f, 0.f);
             v[i] = cmul(z, cmul(wt, __ldg(wi + i)));
         }
     }
@@ -291,7 +317,7 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
         cl.sync();
     }
     if (live) {
-        float2* Xr = a.X + b * a.ld_X;
+        float2* Xr = a.X + Xo;
         const int j0 = rank * chunk;
         for (int j = lt; j < chunk; j += per_trace) Xr[(j0 + j + a.shift) & (a.K - 1)] = zs[pidx(j)];
     }
@@ -362,17 +388,18 @@ void c2c_fill_table(const FftPlan& p, float2* host) {
 }
 
 cudaError_t c2c_launch(const FftPlan& p, const float2* u, int64_t ld_u, int nin, int64_t batch, int shift,
-                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st) {
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
+                       const RaggedItem* items) {
     if (batch == 0) return cudaSuccess;
     C2cKernel k = c2c_kernel_for(p.LZ);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
-    C2cArgs a;
+    C2cArgs a = {};
     a.u = u; a.ld_u = ld_u; a.nin = nin; a.batch = batch;
     a.K = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = p.F;
     a.logChunk = ilog2(p.H / p.C); a.trace_smem = p.trace_smem; a.shift = shift;
-    a.tw = tw; a.tab = tab; a.X = X; a.ld_X = ld_X;
+    a.tw = tw; a.tab = tab; a.X = X; a.ld_X = ld_X; a.items = items;
     const int64_t groups = (batch + p.F - 1) / p.F;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(groups * p.C));
@@ -518,7 +545,7 @@ void fft_fill_table(const FftPlan& p, float2* host) {
 
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
                        const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
-                       int lanes) {
+                       int lanes, const RaggedItem* items) {
     if (batch == 0) return cudaSuccess;
     if (p.H == 0) {   // n_fft == 1
         k_fft_len1<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(x, batch, ld_x, X, ld_X);
@@ -527,12 +554,12 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
     const bool dual = p.dual && lanes != 1;
     FftKernel k = dual ? fft_kernel2_for(p.LZ) : fft_kernel_for(p.LZ, p.emax);
     if (!k) return cudaErrorInvalidValue;
-    FftArgs a;
+    FftArgs a = {};
     a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
     a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C;
     a.logChunk = ilog2(p.H / p.C); a.trace_smem = p.trace_smem;
     a.tw = tw; a.tab = tab;
-    a.X = X; a.ld_X = ld_X;
+    a.X = X; a.ld_X = ld_X; a.items = items;
     const int per_trace = dual ? (p.Rc / 2) * p.T : p.Rc * p.T;
     int F = 1;
     if (p.C == 1) F = (int)std::min<int64_t>(std::max(1, 256 / per_trace), std::max<int64_t>(1, batch));

@@ -31,6 +31,7 @@ struct ZoomArgs {
     const float2* tw;
     float2* X;
     int64_t ld_X;
+    const RaggedItem* items;   // ragged batch: per-trace placement and parameters (else null)
 };
 
 constexpr int kZoomGroup = 4;   // outputs per thread per pass over the taps
@@ -42,49 +43,65 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
     extern __shared__ float4 smem4[];
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x;
-    const int J = a.n_taps - 1;
-    const int D = a.d;
+    int n = a.n, n_taps = a.n_taps, D = a.d, logd = a.logd, lout = a.lout, rs = a.rs;
+    uint64_t Cn = a.Cn;
+    const float* taps = a.taps;
+    int64_t xo = b * a.ld_x, Xo = b * a.ld_X;
+    if (a.items) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+        n_taps = it.n_taps;
+        D = it.d;
+        logd = is_pow2_dev(D) ? ilog2c(D) : -1;
+        lout = it.lout;
+        rs = it.rs;
+        Cn = it.A;
+        taps = a.taps + it.tab_off;
+    }
+    const int J = n_taps - 1;
 
     // shared layout: taps {g.re, g.im, offset} | polyphase x | FFT exchange
     // (the decimated u[m] is staged in the FFT exchange area)
     float4* tap = smem4;
-    float* xs = reinterpret_cast<float*>(smem4 + a.n_taps);
-    float2* s = reinterpret_cast<float2*>(smem4 + a.n_taps) + (D * a.rs + 1) / 2;
+    float* xs = reinterpret_cast<float*>(smem4 + n_taps);
+    float2* s = reinterpret_cast<float2*>(smem4 + n_taps) + (D * rs + 1) / 2;
 
     // complex taps g[k] = h[k] e^{+j 2 pi c k} and their polyphase offsets
-    for (int k = t; k < a.n_taps; k += T) {
-        const float h = __ldg(a.taps + k);
-        const float2 e = unit_fixed(a.Cn * (uint64_t)k, false);
+    for (int k = t; k < n_taps; k += T) {
+        const float h = __ldg(taps + k);
+        const float2 e = unit_fixed(Cn * (uint64_t)k, false);
         const int q = J - k;
-        const int off = (q % D) * a.rs + q / D;
+        const int off = (q % D) * rs + q / D;
         tap[k] = make_float4(h * e.x, h * e.y, __int_as_float(off), 0.f);
     }
     // extended trace xe[j] = x[j - J] (zero outside [0, N)), by phase
-    const float* xr = a.x + b * a.ld_x;
-    const int total = D * a.rs;
-    if (a.logd >= 0) {
+    const float* xr = a.x + xo;
+    const int total = D * rs;
+    if (logd >= 0) {
         const int dm = D - 1;
         for (int j = t; j < total; j += T) {
             const int src = j - J;
-            const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
-            xs[(j & dm) * a.rs + (j >> a.logd)] = xv;
+            const float xv = (src >= 0 && src < n) ? __ldg(xr + src) : 0.f;
+            xs[(j & dm) * rs + (j >> logd)] = xv;
         }
     } else {
         for (int j = t; j < total; j += T) {
             const int src = j - J;
-            const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
-            xs[(j % D) * a.rs + j / D] = xv;
+            const float xv = (src >= 0 && src < n) ? __ldg(xr + src) : 0.f;
+            xs[(j % D) * rs + j / D] = xv;
         }
     }
     __syncthreads();
 
     // FIR + decimate: groups of four outputs m = t + T (4 g + u)
-    for (int m0 = t; m0 < a.lout; m0 += kZoomGroup * T) {
+    for (int m0 = t; m0 < lout; m0 += kZoomGroup * T) {
         float re[kZoomGroup], im[kZoomGroup];
 #pragma unroll
         for (int u = 0; u < kZoomGroup; ++u) re[u] = im[u] = 0.f;
         const float* xm = xs + m0;
-        for (int k = 0; k < a.n_taps; ++k) {
+        for (int k = 0; k < n_taps; ++k) {
             const float4 g = tap[k];
             const float* xk = xm + __float_as_int(g.z);
 #pragma unroll
@@ -97,8 +114,8 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
 #pragma unroll
         for (int u = 0; u < kZoomGroup; ++u) {
             const int m = m0 + u * T;
-            if (m < a.lout) {
-                const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
+            if (m < lout) {
+                const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
                 s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
             }
         }
@@ -108,10 +125,10 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int m = t + T * i;
-        v[i] = m < a.lout ? s[pidx(m)] : make_float2(0.f, 0.f);
+        v[i] = m < lout ? s[pidx(m)] : make_float2(0.f, 0.f);
     }
     FFT::run(v, s, t, a.tw);
-    float2* Xr = a.X + b * a.ld_X;
+    float2* Xr = a.X + Xo;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int j = t + T * i;
@@ -221,6 +238,7 @@ struct FirArgs {
     uint64_t Cn;
     float2* u;
     int64_t ld_u;
+    const RaggedItem* items;   // ragged batch (else null)
 };
 
 __global__ void __launch_bounds__(kFirChunk) k_zoom_fir(FirArgs a) {
@@ -228,41 +246,59 @@ __global__ void __launch_bounds__(kFirChunk) k_zoom_fir(FirArgs a) {
     const int t = threadIdx.x;
     const int64_t b = blockIdx.x / a.chunks;
     const int m0 = (int)(blockIdx.x % a.chunks) * kFirChunk;
-    const int J = a.n_taps - 1;
-    const int D = a.d;
+    int n = a.n, n_taps = a.n_taps, D = a.d, logd = a.logd, lout = a.lout, rs = a.rs;
+    uint64_t Cn = a.Cn;
+    const float* taps = a.taps;
+    int64_t xo = b * a.ld_x, uo = b * a.ld_u;
+    if (a.items) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        uo = it.u_off;
+        n = it.n;
+        n_taps = it.n_taps;
+        D = it.d;
+        logd = is_pow2_dev(D) ? ilog2c(D) : -1;
+        lout = it.lout;
+        rs = kFirChunk + (n_taps - 1) / D + 2;
+        rs += (rs & 1) ^ 1;
+        Cn = it.A;
+        taps = a.taps + it.tab_off;
+        if (m0 >= lout) return;            // this trace has fewer chunks (whole CTA)
+    }
+    const int J = n_taps - 1;
     float4* tap = smem4;
-    float* xs = reinterpret_cast<float*>(smem4 + a.n_taps);
+    float* xs = reinterpret_cast<float*>(smem4 + n_taps);
 
-    for (int k = t; k < a.n_taps; k += kFirChunk) {
-        const float h = __ldg(a.taps + k);
-        const float2 e = unit_fixed(a.Cn * (uint64_t)k, false);
+    for (int k = t; k < n_taps; k += kFirChunk) {
+        const float h = __ldg(taps + k);
+        const float2 e = unit_fixed(Cn * (uint64_t)k, false);
         const int q = J - k;
-        tap[k] = make_float4(h * e.x, h * e.y, __int_as_float((q % D) * a.rs + q / D), 0.f);
+        tap[k] = make_float4(h * e.x, h * e.y, __int_as_float((q % D) * rs + q / D), 0.f);
     }
     // window of the extended trace for outputs m0 .. m0 + kFirChunk - 1:
     // local index jj = j - m0 D, sample x[j - J]
-    const float* xr = a.x + b * a.ld_x;
-    const int total = D * a.rs;
+    const float* xr = a.x + xo;
+    const int total = D * rs;
     const int64_t base = (int64_t)m0 * D - J;
     for (int jj = t; jj < total; jj += kFirChunk) {
         const int64_t src = base + jj;
-        const float xv = (src >= 0 && src < a.n) ? __ldg(xr + src) : 0.f;
-        const int slot = a.logd >= 0 ? (jj & (D - 1)) * a.rs + (jj >> a.logd) : (jj % D) * a.rs + jj / D;
+        const float xv = (src >= 0 && src < n) ? __ldg(xr + src) : 0.f;
+        const int slot = logd >= 0 ? (jj & (D - 1)) * rs + (jj >> logd) : (jj % D) * rs + jj / D;
         xs[slot] = xv;
     }
     __syncthreads();
     const int m = m0 + t;
-    if (m < a.lout) {
+    if (m < lout) {
         float re = 0.f, im = 0.f;
         const float* xm = xs + t;
-        for (int k = 0; k < a.n_taps; ++k) {
+        for (int k = 0; k < n_taps; ++k) {
             const float4 g = tap[k];
             const float xv = xm[__float_as_int(g.z)];
             re = fmaf(g.x, xv, re);
             im = fmaf(g.y, xv, im);
         }
-        const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
-        a.u[b * a.ld_u + m] = cmul(make_float2(re, im), rot);
+        const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
+        a.u[uo + m] = cmul(make_float2(re, im), rot);
     }
 }
 
@@ -294,7 +330,7 @@ cudaError_t zoom_big_launch(const ZoomPlan& p, const float* x, int64_t batch, in
                             float2* work, const float2* tw, const float2* tab, float2* X, int64_t ld_X,
                             cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
-    FirArgs a;
+    FirArgs a = {};
     a.x = x; a.batch = batch; a.n = p.n; a.ld_x = ld_x; a.taps = taps;
     a.n_taps = p.n_taps; a.d = p.d; a.logd = is_pow2(p.d) ? ilog2(p.d) : -1; a.lout = p.lout; a.rs = p.rs;
     a.chunks = (p.lout + kFirChunk - 1) / kFirChunk; a.Cn = p.Cn;
@@ -392,13 +428,62 @@ cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_
     const size_t smem = dual ? p.smem2 : p.smem;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    ZoomArgs a;
+    ZoomArgs a = {};
     a.x = x; a.batch = batch; a.n = p.n; a.ld_x = ld_x; a.taps = taps;
     a.n_taps = p.n_taps; a.d = p.d; a.logd = is_pow2(p.d) ? ilog2(p.d) : -1;
     a.lout = p.lout; a.rs = p.rs; a.Cn = p.Cn; a.tw = tw;
     a.X = X; a.ld_X = ld_X;
     const int64_t grid = dual ? (batch + 1) / 2 : batch;
     k<<<(unsigned)grid, p.threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches (per-trace parameters from RaggedItem).
+
+int zoom_rows(int64_t lout, int64_t n_taps, int64_t d) {
+    int64_t rs = (lout - 1) + (n_taps - 1) / d + 2;
+    return (int)(rs | 1);
+}
+
+size_t zoom_smem_for(int n_taps, int d, int rs, int K) {
+    const int E = K < 16 ? K : 16;
+    const int T = K / E;
+    return (size_t)n_taps * 16 + (size_t)((d * rs + 1) / 2) * 8 + (size_t)padded_len(K) * 8 +
+           (size_t)kZoomGroup * T * 4;
+}
+
+int fir_rows(int64_t n_taps, int64_t d) {
+    int64_t rs = kFirChunk + (n_taps - 1) / d + 2;
+    return (int)(rs | 1);
+}
+
+size_t fir_smem_for(int n_taps, int d) { return (size_t)n_taps * 16 + (size_t)d * fir_rows(n_taps, d) * 4; }
+
+int fir_chunk() { return kFirChunk; }
+
+cudaError_t zoom_ragged_launch(int K, const RaggedItem* items, int64_t count, size_t smem, const float* x_pool,
+                               const float* taps_pool, const float2* tw, float2* X_pool, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    ZoomKernel k = zoom_kernel_for(K);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ZoomArgs a = {};
+    a.x = x_pool; a.batch = count; a.taps = taps_pool; a.tw = tw; a.X = X_pool; a.items = items;
+    const int E = K < 16 ? K : 16;
+    k<<<(unsigned)count, K / E, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t zoom_fir_ragged_launch(const RaggedItem* items, int64_t count, int chunks_max, size_t smem,
+                                   const float* x_pool, const float* taps_pool, float2* work, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_zoom_fir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    FirArgs a = {};
+    a.x = x_pool; a.batch = count; a.taps = taps_pool; a.chunks = chunks_max; a.u = work; a.items = items;
+    k_zoom_fir<<<(unsigned)(count * chunks_max), kFirChunk, smem, st>>>(a);
     return cudaGetLastError();
 }
 

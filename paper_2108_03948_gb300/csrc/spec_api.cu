@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "fft_block.cuh"
 #include "spec.h"
 #include "spec_internal.h"
@@ -66,31 +67,6 @@ uint64_t cycles_to_fixed(double cycles) {
 }  // namespace spec
 
 using namespace spec;
-
-struct CztEntry {
-    CztTables t;
-    void* mem = nullptr;
-    cudaEvent_t ready = nullptr;
-    uint64_t last_use = 0;
-};
-
-struct FftEntry {
-    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables
-    int H = 0, LZ = 0;
-    float2* tab = nullptr;
-};
-
-struct spec_ctx {
-    int device = 0;
-    std::string err;
-    float2* block_tw = nullptr;          // BlockFFT twiddles of every size
-    int lanes = 1;                       // 1: one FFT per thread group; 2: two packed lanes where possible
-    std::vector<FftEntry> fft;
-    std::vector<CztEntry> czt;
-    uint64_t tick = 0;
-    void* stage[4] = {nullptr, nullptr, nullptr, nullptr};   // x, X, taps, workspace
-    size_t stage_bytes[4] = {0, 0, 0, 0};
-};
 
 static std::string g_create_err;
 static const size_t kCztCacheMax = 64;
@@ -218,7 +194,7 @@ spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, 
 // complex FFT (kind 1), built on the host in float64 and cached.
 spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab) {
     for (auto& it : c->fft)
-        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ) {
+        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax) {
             *tab = it.tab;
             return SPEC_OK;
         }
@@ -226,6 +202,7 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     ne.kind = kind;
     ne.H = p.H;
     ne.LZ = p.LZ;
+    ne.emax = p.emax;
     std::vector<float2> host((size_t)(kind == 0 ? fft_table_entries(p) : c2c_table_entries(p)));
     if (kind == 0) fft_fill_table(p, host.data());
     else c2c_fill_table(p, host.data());
@@ -241,6 +218,15 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
 }
 
 }  // namespace
+
+namespace spec {
+spec_status ctx_fail(spec_ctx* c, spec_status s, const std::string& why) { return fail(c, s, why); }
+spec_status ctx_cuda_fail(spec_ctx* c, cudaError_t e, const char* what) { return cuda_fail(c, e, what); }
+bool ctx_is_device_ptr(const void* p) { return is_device_ptr(p); }
+spec_status ctx_plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab) {
+    return plan_table(c, kind, p, tab);
+}
+}  // namespace spec
 
 extern "C" {
 
@@ -304,6 +290,7 @@ void spec_ctx_destroy(spec_ctx* c) {
         }
         for (auto& en : c->fft)
             if (en.tab) cudaFree(en.tab);
+        for (RaggedPlan* rp : c->ragged) ragged_plan_free(rp);
         if (c->block_tw) cudaFree(c->block_tw);
         for (int i = 0; i < 4; ++i)
             if (c->stage[i]) cudaFree(c->stage[i]);

@@ -26,6 +26,19 @@ inline int ilog2(int64_t v) {
     return l;
 }
 
+// Placement and parameters of one trace of a ragged batch (device array,
+// indexed by the trace's position in its class).  Fields a kind does not use
+// are zero.
+struct RaggedItem {
+    int64_t x_off;     // first sample in the x pool (floats)
+    int64_t out_off;   // first bin in the X pool (complex elements)
+    int64_t tab_off;   // CZT: its tables (pre | V | post); Zoom: first tap in the taps pool
+    int64_t u_off;     // Zoom, large path: its decimated samples in the workspace
+    uint64_t A, B;     // CZT: frac(f1/fs), frac(step/(2 fs)); Zoom: A = frac(f_N/fs)
+    int32_t n, m;      // samples; CZT points
+    int32_t d, n_taps, lout, rs;   // Zoom
+};
+
 // Phase in cycles -> 64-bit fixed-point fraction (exact wrap-around modulo
 // one cycle under unsigned multiplication).
 uint64_t cycles_to_fixed(double cycles);
@@ -55,7 +68,7 @@ void fft_fill_table(const FftPlan& p, float2* host);
 // used where the plan allows it.
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
                        const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
-                       int lanes);
+                       int lanes, const RaggedItem* items = nullptr);
 
 // Pruned complex FFT with rotated store (k_fft.cu), planned in an FftPlan
 // with H = K: Y[(j + shift) mod K] = FFT_K(u zero-padded)[j].
@@ -63,7 +76,8 @@ bool c2c_plan(int64_t batch, int64_t nin, int64_t K, FftPlan* p, std::string* wh
 int c2c_table_entries(const FftPlan& p);
 void c2c_fill_table(const FftPlan& p, float2* host);
 cudaError_t c2c_launch(const FftPlan& p, const float2* u, int64_t ld_u, int nin, int64_t batch, int shift,
-                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st);
+                       const float2* tw, const float2* tab, float2* X, int64_t ld_X, cudaStream_t st,
+                       const RaggedItem* items = nullptr);
 
 // BlockFFT twiddle tables of every size up to kMaxBlockFFT in one buffer:
 // first the radix-16 layouts (sizes 32 ..), then the radix-32 ones (64 ..).
@@ -115,5 +129,20 @@ cudaError_t zoom_big_launch(const ZoomPlan& p, const float* x, int64_t batch, in
 cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_t ld_x,
                         const float* taps, const float2* tw, float2* X, int64_t ld_X, cudaStream_t st,
                         int lanes);
+
+// ---- ragged batches (ragged.cu drives these) -------------------------------
+cudaError_t czt_ragged_tables(int L, const RaggedItem* items, int64_t count, float2* tables, const float2* tw,
+                              cudaStream_t st);
+cudaError_t czt_ragged_launch(int L, const RaggedItem* items, int64_t count, const float* x_pool,
+                              const float2* tables, const float2* tw, float2* X_pool, cudaStream_t st);
+int zoom_rows(int64_t lout, int64_t n_taps, int64_t d);
+size_t zoom_smem_for(int n_taps, int d, int rs, int K);
+int fir_rows(int64_t n_taps, int64_t d);
+size_t fir_smem_for(int n_taps, int d);
+int fir_chunk();
+cudaError_t zoom_ragged_launch(int K, const RaggedItem* items, int64_t count, size_t smem, const float* x_pool,
+                               const float* taps_pool, const float2* tw, float2* X_pool, cudaStream_t st);
+cudaError_t zoom_fir_ragged_launch(const RaggedItem* items, int64_t count, int chunks_max, size_t smem,
+                                   const float* x_pool, const float* taps_pool, float2* work, cudaStream_t st);
 
 }  // namespace spec

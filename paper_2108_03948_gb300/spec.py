@@ -26,8 +26,18 @@ _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "
            SPEC_EUNSUPPORTED: "SPEC_EUNSUPPORTED", SPEC_ETIMEOUT: "SPEC_ETIMEOUT"}
 
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
-           "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static",
+           "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static", "spec_ragged",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
+
+SPEC_KIND_FFT, SPEC_KIND_CZT, SPEC_KIND_ZOOM = 0, 1, 2
+
+
+class spec_desc(C.Structure):
+    """One trace of a ragged batch (include/spec.h)."""
+    _fields_ = [("x_off", C.c_int64), ("n", C.c_int64), ("out_off", C.c_int64), ("f1", C.c_double),
+                ("f2", C.c_double), ("n_fft", C.c_int64), ("m", C.c_int64), ("d", C.c_int64),
+                ("taps_off", C.c_int64), ("n_taps", C.c_int64)]
+
 
 _lib = None
 
@@ -61,6 +71,8 @@ def lib():
     L.spec_czt.restype = C.c_int
     L.spec_zoom.argtypes = [vp, fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, i64, fp, i64, vp]
     L.spec_zoom.restype = C.c_int
+    L.spec_ragged.argtypes = [vp, C.c_int, C.POINTER(spec_desc), i64, dbl, fp, fp, fp, vp]
+    L.spec_ragged.restype = C.c_int
     L.spec_czt_static.argtypes = [fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, vp]
     L.spec_czt_static.restype = C.c_int
     L.spec_zeros_for_delta.argtypes = [dbl, i64, dbl]
@@ -201,6 +213,21 @@ def spec_zoom(ctx: Context, x, fs: float, f1: float, f2: float, d: int, taps, n_
     ctx.check(lib().spec_zoom(ctx.handle, px, batch, n, ld_x, float(fs), float(f1), float(f2), int(d),
                               pt, nt, int(n_fft), po, ld_o, st if stream is None else stream))
     return o
+
+
+def spec_ragged(ctx: Context, kind: int, descs, fs: float, x_pool, X_pool, taps_pool=None, stream=None):
+    """Ragged batch: descs is a sequence of spec_desc (or dicts of its fields);
+    pools are CUDA tensors (x float32, X complex64, taps float32)."""
+    import torch
+    n = len(descs)
+    arr = (spec_desc * max(1, n))()
+    for i, dsc in enumerate(descs):
+        arr[i] = dsc if isinstance(dsc, spec_desc) else spec_desc(**dsc)
+    st = torch.cuda.current_stream(x_pool.device).cuda_stream if stream is None else stream
+    ctx.check(lib().spec_ragged(ctx.handle, int(kind), arr, n, float(fs), x_pool.data_ptr(),
+                                taps_pool.data_ptr() if taps_pool is not None else None,
+                                X_pool.data_ptr(), st))
+    return X_pool
 
 
 # ---------------------------------------------------------------- helpers ---

@@ -1,0 +1,134 @@
+"""Ragged batches (spec_ragged): traces with their own length, band, point
+count, decimation and taps in one call.  Every trace must match the same
+trace run alone through spec_fft / spec_czt / spec_zoom to 1e-6 relative L2
+(the same kernels and tables, except that the plan's autotuner may pick a
+different variant -- lanes or pass radix -- whose rounding differs in the last
+bits), and a sample is checked against the FP64 oracle (relative L2 <= 1e-5
+per spectrum).  The plan's CUDA graph replay is bit-identical to its first
+run, and the graph is re-captured when the pools move."""
+import numpy as np
+import pytest
+
+from oracle import spec_oracle as O
+from paper_2108_03948_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+FS = synth.FS
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2108_03948_gb300 import build
+    build.build()
+    from paper_2108_03948_gb300 import spec
+    return spec
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.Context(0)
+    yield c
+    c.close()
+
+
+def workload(count, seed=5):
+    """Workload-2-shaped traces and parameters, with some extremes mixed in."""
+    rg = synth.ragged_params(count)
+    items = list(rg.items)
+    items[0] = synth.RaggedTrace(8192, 65536, 0.1e12, 3.9e12, 4096, 2, 127)    # largest of each
+    items[1] = synth.RaggedTrace(1000, 8192, 0.1e12, 0.6e12, 256, 16, 31)      # smallest
+    traces = [synth.ragged_trace(i, it) for i, it in enumerate(items)]
+    return items, traces
+
+
+def pools(items, traces, kind):
+    xo, x_all = [], []
+    off = 0
+    for t in traces:
+        xo.append(off)
+        x_all.append(t)
+        off += len(t) + 3                              # gaps between traces
+        x_all.append(np.zeros(3, np.float32))
+    x_pool = torch.from_numpy(np.concatenate(x_all)).cuda()
+    bins = []
+    for it in items:
+        bins.append(it.n_fft // 2 + 1 if kind == 0 else it.m if kind == 1 else it.n_fft // it.d)
+    oo = np.concatenate([[0], np.cumsum(bins)[:-1]]).astype(np.int64)
+    X_pool = torch.full((int(np.sum(bins)),), float("nan"), dtype=torch.complex64, device="cuda")
+    taps, to = [], []
+    toff = 0
+    for it in items:
+        h = O.design_lowpass(it.n_taps, it.d).astype(np.float32)
+        taps.append(h)
+        to.append(toff)
+        toff += len(h)
+    taps_pool = torch.from_numpy(np.concatenate(taps)).cuda()
+    descs = [dict(x_off=int(xo[i]), n=it.n, out_off=int(oo[i]), f1=it.f1, f2=it.f2, n_fft=it.n_fft, m=it.m,
+                  d=it.d, taps_off=int(to[i]), n_taps=it.n_taps) for i, it in enumerate(items)]
+    return descs, x_pool, X_pool, taps_pool, bins, taps
+
+
+def single(S, ctx, kind, it, x, h):
+    xd = torch.from_numpy(x[None, :]).cuda()
+    if kind == 0:
+        return S.spec_fft(ctx, xd, FS, it.n_fft)[0]
+    if kind == 1:
+        return S.spec_czt(ctx, xd, FS, it.f1, it.f2, it.m)[0]
+    return S.spec_zoom(ctx, xd, FS, it.f1, it.f2, it.d, torch.from_numpy(h).cuda(), it.n_fft)[0]
+
+
+def oracle(kind, it, x, h):
+    if kind == 0:
+        return O.fft_padded(x, it.n_fft)[0]
+    if kind == 1:
+        return O.czt(x, FS, it.f1, it.f2, it.m)[0]
+    return O.zoom(x, FS, it.f1, it.f2, it.d, h, it.n_fft)[0]
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_ragged_matches_single_calls_and_oracle(S, ctx, kind):
+    items, traces = workload(48)
+    descs, x_pool, X_pool, taps_pool, bins, taps = pools(items, traces, kind)
+    S.spec_ragged(ctx, kind, descs, FS, x_pool, X_pool, taps_pool)
+    first = X_pool.clone()
+    S.spec_ragged(ctx, kind, descs, FS, x_pool, X_pool, taps_pool)      # graph replay
+    torch.cuda.synchronize()
+    assert torch.equal(torch.view_as_real(first), torch.view_as_real(X_pool))
+    got = X_pool.cpu().numpy()
+    for i, it in enumerate(items):
+        o, nb = descs[i]["out_off"], bins[i]
+        ref = single(S, ctx, kind, it, traces[i], taps[i]).cpu().numpy()
+        d = np.linalg.norm(got[o:o + nb] - ref) / np.linalg.norm(ref)
+        assert d <= 1e-6, (i, d)
+        if i < 6 or i % 8 == 0:
+            r = oracle(kind, it, traces[i], taps[i])
+            err = np.linalg.norm(got[o:o + nb] - r) / np.linalg.norm(r)
+            assert err <= TOL, (i, err)
+
+
+def test_ragged_recaptures_when_pools_move(S, ctx):
+    items, traces = workload(12)
+    descs, x_pool, X_pool, taps_pool, bins, taps = pools(items, traces, 1)
+    S.spec_ragged(ctx, 1, descs, FS, x_pool, X_pool, taps_pool)
+    x2 = x_pool.clone()
+    X2 = torch.zeros_like(X_pool)
+    S.spec_ragged(ctx, 1, descs, FS, x2, X2, taps_pool)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.view_as_real(X_pool), torch.view_as_real(X2))
+
+
+def test_ragged_rejects_bad_descriptors(S, ctx):
+    lib = S.lib()
+    x = torch.zeros(64, device="cuda")
+    X = torch.zeros(64, dtype=torch.complex64, device="cuda")
+    bad = (S.spec_desc * 2)(S.spec_desc(0, 64, 0, 0, 0, 64, 0, 0, 0, 0), S.spec_desc(0, 64, 0, 0, 0, 48, 0, 0, 0, 0))
+    st = lib.spec_ragged(ctx.handle, 0, bad, 2, FS, x.data_ptr(), None, X.data_ptr(), None)
+    assert st == S.SPEC_EINVAL
+    assert b"descriptor 1" in lib.spec_last_error(ctx.handle)
+    # host pools are refused
+    xh = np.zeros(64, np.float32)
+    st = lib.spec_ragged(ctx.handle, 0, bad, 1, FS, xh.ctypes.data, None, X.data_ptr(), None)
+    assert st == S.SPEC_EINVAL
