@@ -1,11 +1,16 @@
 """Benchmark: batched spectral estimation of THz-TDS traces on one GB300.
 
 A step is one pass of the whole hot path over one batch: the zero-padded FFT,
-the chirp-z transform (Bluestein) and the Zoom FFT of every trace.  The
-workload is 4096 synthetic traces of N = 2048 float32 samples at fs = 20 THz
-(FFT to 16384, CZT 0.2-2.5 THz at M = 1024, Zoom FFT at 1.35 THz with D = 4
-and a 63-tap Hamming low-pass), inputs resident in HBM.  The metric is
-spectral bins per second (FFT N_FFT/2+1, CZT M, Zoom N_FFT/D bins per trace).
+the chirp-z transform (Bluestein) and the Zoom FFT of every trace, inputs
+resident in HBM.  The metric is spectral bins per second (FFT N_FFT/2+1,
+CZT M, Zoom N_FFT/D bins per trace).
+
+Workloads (``--workload``):
+  1 (default) 4096 synthetic traces of N = 2048 float32 samples at fs = 20 THz
+    -- FFT to 16384, CZT 0.2-2.5 THz at M = 1024, Zoom FFT at 1.35 THz with
+    D = 4 and a 63-tap Hamming low-pass -- one launch per transform;
+  2 10000 ragged traces (N 1000-8192, per-trace band, M, D, taps;
+    N_FFT = 8 nextpow2(N)) -- one CUDA-graph launch per transform.
 
 Timing: W warm-up steps, then K steps; before each step a 256 MB buffer is
 written to flush L2 (outside the per-step events).  Every transform is
@@ -36,9 +41,13 @@ if ROOT not in sys.path:
 from paper_2108_03948_gb300 import synth  # noqa: E402
 
 METRIC = "spectral bins/s per transform at ≤1e-5 rel L2 vs FP64; % HBM/tensor roofline"
-WORKLOAD = 1
 # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+W1_NAME = ("4096 THz traces, N=2048 float32, fs=20 THz; FFT to 16384, CZT 0.2-2.5 THz M=1024, "
+           "Zoom 1.35 THz D=4 63-tap Hamming; one launch per transform")
+W2_NAME = ("10000 ragged THz traces, N 1000-8192, fs=20 THz, N_FFT=8 nextpow2(N); per-trace CZT band "
+           "(f1 0.1-1.0 THz, width 0.5-3.0 THz, M 256-4096) and Zoom (D 2-16, 31-127 taps); "
+           "one CUDA-graph launch per transform")
 
 
 def env_rank():
@@ -72,24 +81,66 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def workload_sizes(cfg):
-    """Per-trace bins, algorithmic bytes and flops of each transform."""
-    n = cfg.n
-    L = max(16, 1 << (n + cfg.czt_m - 2).bit_length())
-    K = cfg.zoom_n_fft // cfg.zoom_d
-    lout = (n + cfg.zoom_taps - 1 + cfg.zoom_d - 1) // cfg.zoom_d
-    return {
-        "fft": {"bins": cfg.n_fft // 2 + 1, "bytes": 4 * n + 8 * (cfg.n_fft // 2 + 1),
-                "flops": 2.5 * cfg.n_fft * np.log2(cfg.n_fft)},
-        "czt": {"bins": cfg.czt_m, "bytes": 4 * n + 8 * cfg.czt_m,
-                "flops": 2 * 5 * L * np.log2(L) + 6 * (n + L + cfg.czt_m)},
-        "zoom": {"bins": K, "bytes": 4 * n + 8 * K,
-                 "flops": 4 * lout * cfg.zoom_taps + 6 * n + 5 * K * np.log2(K)},
-    }
+def trace_cost(kind, n, n_fft=0, m=0, d=1, taps=1):
+    """Bins, algorithmic bytes (input read once, output written once) and
+    algorithmic flops of one trace."""
+    if kind == "fft":
+        return n_fft // 2 + 1, 4 * n + 8 * (n_fft // 2 + 1), 2.5 * n_fft * np.log2(max(n_fft, 2))
+    if kind == "czt":
+        L = max(16, 1 << (n + m - 2).bit_length())
+        return m, 4 * n + 8 * m, 2 * 5 * L * np.log2(L) + 6 * (n + L + m)
+    K = n_fft // d
+    lout = (n + taps - 1 + d - 1) // d
+    return K, 4 * n + 8 * K, 4 * lout * taps + 6 * n + 5 * K * np.log2(max(K, 2))
+
+
+class NvmlClocks:
+    """SM clock, power and clock-event reasons read through NVML (ctypes, no
+    extra package) every millisecond from a thread, so that even a timed region
+    of a few milliseconds is sampled.  Reading is all it does."""
+    SM = 1                                           # NVML_CLOCK_SM
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        bus = self._bus_id(cuda_index)
+        ok = bus is not None and self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(cuda_index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        u = ctypes.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(u))
+        self.max_mhz = float(u.value)
+
+    @staticmethod
+    def _bus_id(cuda_index):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(cuda_index)
+            return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+        except (AttributeError, RuntimeError, AssertionError):
+            return None
+
+    def sample(self):
+        c = self.c
+        mhz, mw, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, c.byref(mhz))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, c.byref(mw))
+        self.reasons_fn(self.h, c.byref(rs))
+        return float(mhz.value), mw.value / 1e3, int(rs.value)
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """Clocks and throttle reasons during the timed region: NVML every 1 ms
+    when the library loads, else nvidia-smi every 100 ms.  Samples go to a CSV
+    beside the run's other output."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -98,18 +149,43 @@ class ClockSampler:
         self.path = path
         self.index = index
         self.proc = None
+        self.nvml = None
+        self.rows = []
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = NvmlClocks(self.index)
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.stop = threading.Event()
+
+            def loop():
+                while not self.stop.is_set():
+                    self.rows.append(self.nvml.sample())
+                    time.sleep(0.001)
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return self
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self.stop.set()
+            self.thread.join()
+            self.rows.append(self.nvml.sample())
+            with open(self.path, "w") as f:
+                f.write("sm_mhz,sm_max_mhz,power_w,reasons_mask\n")
+                for mhz, w, rs in self.rows:
+                    f.write(f"{mhz:.0f},{self.nvml.max_mhz:.0f},{w:.1f},{rs:#x}\n")
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -119,8 +195,15 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        if self.nvml is not None:
+            sm = [r[0] for r in self.rows]
+            smax = self.nvml.max_mhz
+            reasons = sorted({name for r in self.rows for bit, name in NvmlClocks.BITS.items() if r[2] & bit})
+            loaded = [s for s in sm if s > 0.5 * smax] or sm
+            return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                    "samples": len(self.rows), "source": "NVML, 1 ms"}
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
         rows = []
         with open(self.path) as f:
             for line in f:
@@ -135,26 +218,7 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         loaded = [s for s in sm if s > 0.5 * smax] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
-                "samples": len(rows)}
-
-
-def oracle_sample(cfg, n_traces):
-    """Time the FP64 oracle on the first n_traces of the workload.
-
-    Returns (bins, seconds, outputs); this is the CPU-baseline leg, the only
-    place the benchmark runs the oracle."""
-    from oracle import spec_oracle as O
-    x = synth.batch_traces(WORKLOAD, range(n_traces))
-    taps = O.design_lowpass(cfg.zoom_taps, cfg.zoom_d)
-    t0 = time.perf_counter()
-    outs = {
-        "fft": O.fft_padded(x, cfg.n_fft),
-        "czt": O.czt(x, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m),
-        "zoom": O.zoom(x, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, taps, cfg.zoom_n_fft),
-    }
-    dt = time.perf_counter() - t0
-    bins = n_traces * (cfg.n_fft // 2 + 1 + cfg.czt_m + cfg.zoom_n_fft // cfg.zoom_d)
-    return bins, dt, outs
+                "samples": len(rows), "source": "nvidia-smi, 100 ms"}
 
 
 def cpu_threads():
@@ -168,34 +232,251 @@ def cpu_threads():
     return os.cpu_count() or 1
 
 
+# ------------------------------------------------------------------ oracle --
+# The CPU-baseline / reference legs: the only places the benchmark runs the
+# FP64 oracle.
+
+def oracle_uniform(cfg, n_traces):
+    """Time the oracle on the first n_traces of workload 1: (bins, s, outputs)."""
+    from oracle import spec_oracle as O
+    x = synth.batch_traces(1, range(n_traces))
+    taps = O.design_lowpass(cfg.zoom_taps, cfg.zoom_d)
+    t0 = time.perf_counter()
+    outs = {
+        "fft": O.fft_padded(x, cfg.n_fft),
+        "czt": O.czt(x, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m),
+        "zoom": O.zoom(x, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, taps, cfg.zoom_n_fft),
+    }
+    dt = time.perf_counter() - t0
+    bins = n_traces * (cfg.n_fft // 2 + 1 + cfg.czt_m + cfg.zoom_n_fft // cfg.zoom_d)
+    return bins, dt, outs
+
+
+def oracle_ragged(items, traces, pick, max_bins=None):
+    """Time the oracle on the picked ragged traces: (bins, s, {kind: {i: out}}).
+    With ``max_bins`` each transform evaluates at most that many of its bins,
+    evenly strided over its range (the oracle evaluates bins one by one, so a
+    subset is a proportional sample of its work)."""
+    from oracle import spec_oracle as O
+
+    def sub(total):
+        if max_bins is None or total <= max_bins:
+            return np.arange(total)
+        return np.unique(np.linspace(0, total - 1, max_bins).round().astype(np.int64))
+
+    outs = {"fft": {}, "czt": {}, "zoom": {}}
+    bins = 0
+    t0 = time.perf_counter()
+    for i in pick:
+        it, x = items[i], traces[i]
+        h = O.design_lowpass(it.n_taps, it.d)
+        kf, kc, kz = sub(it.n_fft // 2 + 1), sub(it.m), sub(it.n_fft // it.d)
+        outs["fft"][i] = O.fft_padded_bins(x, it.n_fft, kf)[0]
+        outs["czt"][i] = O.czt_bins(x, synth.FS, it.f1, it.f2, it.m, kc)[0]
+        outs["zoom"][i] = O.zoom_bins(x, synth.FS, it.f1, it.f2, it.d, h, it.n_fft, kz)[0]
+        bins += len(kf) + len(kc) + len(kz)
+    return bins, time.perf_counter() - t0, outs
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    cfg = synth.UNIFORM[WORKLOAD]
-    sample = 1024
-    for _ in range(max(0, args.warmup)):
-        oracle_sample(cfg, 16)
     times, bins_tot = [], 0
-    for _ in range(args.steps):
-        b, dt, _ = oracle_sample(cfg, sample)
-        times.append(dt)
-        bins_tot += b
+    steps = max(1, args.steps)
+    if args.workload == 2:
+        # Per step one ragged trace, a different one each step (stride 9973
+        # through the 10000) so that the sample spans the mix of sizes, and
+        # per transform an evenly strided subset of its bins; the subset
+        # shrinks as K grows so that the run stays near a fixed CPU budget.
+        rg = synth.ragged_params(10000)
+        nb = max(64, min(8192, 102400 // steps))
+        picks = [(9973 * s) % 10000 for s in range(steps)]
+        traces = {i: synth.ragged_trace(i, rg.items[i]) for i in sorted(set(picks) | {0})}
+        for _ in range(max(0, args.warmup)):
+            oracle_ragged(rg.items, traces, [0], 64)
+        for i in picks:
+            b, dt, _ = oracle_ragged(rg.items, traces, [i], nb)
+            times.append(dt)
+            bins_tot += b
+        sample, name = f"1 of 10000 ragged traces per step (a new one each step), at most {nb} evenly strided " \
+                       "bins of each of the three transforms", W2_NAME
+    else:
+        # Traces per step shrink as K grows so that the run stays near a
+        # fixed CPU budget (about 40k traces in total).
+        cfg = synth.UNIFORM[1]
+        per = max(8, min(1024, 40960 // steps))
+        for _ in range(max(0, args.warmup)):
+            oracle_uniform(cfg, 8)
+        for _ in range(args.steps):
+            b, dt, _ = oracle_uniform(cfg, per)
+            times.append(dt)
+            bins_tot += b
+        sample, name = f"{per} of 4096 traces per step, all bins of all three transforms", W1_NAME
     value = bins_tot / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "bins/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": "4096 THz traces, N=2048, fs=20 THz; FFT 16384, CZT 0.2-2.5 THz M=1024, "
-                               "Zoom 1.35 THz D=4 63 taps", "sample_traces_per_step": sample},
+        "data": "synthetic", "config": {"workload": name, "sample": sample},
         "cpu_baseline": {"value": value, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
-                         "sample": f"{sample} of 4096 traces per step, all bins of all three transforms"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "bins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
+
+# --------------------------------------------------------------- workloads --
+
+class Uniform:
+    """Workload 1: 4096 traces x 2048 samples, one launch per transform."""
+
+    def __init__(self, spec, ctx, dev):
+        import torch
+        cfg = self.cfg = synth.UNIFORM[1]
+        B = self.B = cfg.batch
+        self.spec, self.ctx = spec, ctx
+        self.x = synth.batch_traces(1, range(B))
+        self.xd = torch.from_numpy(self.x).to(dev)
+        self.taps_h = spec.spec_design_lowpass(cfg.zoom_taps, cfg.zoom_d)
+        self.taps_d = torch.from_numpy(self.taps_h).to(dev)
+        c = {"fft": trace_cost("fft", cfg.n, cfg.n_fft),
+             "czt": trace_cost("czt", cfg.n, m=cfg.czt_m),
+             "zoom": trace_cost("zoom", cfg.n, cfg.zoom_n_fft, d=cfg.zoom_d, taps=cfg.zoom_taps)}
+        self.bins = {k: B * v[0] for k, v in c.items()}
+        self.bytes = {k: B * v[1] for k, v in c.items()}
+        self.flops = {k: B * v[2] for k, v in c.items()}
+        self.out = {k: torch.empty((B, c[k][0]), dtype=torch.complex64, device=dev) for k in c}
+        self.name = W1_NAME
+
+    def parts(self):
+        s, ctx, cfg, o = self.spec, self.ctx, self.cfg, self.out
+        return [("fft", lambda: s.spec_fft(ctx, self.xd, cfg.fs, cfg.n_fft, out=o["fft"])),
+                ("czt", lambda: s.spec_czt(ctx, self.xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, out=o["czt"])),
+                ("zoom", lambda: s.spec_zoom(ctx, self.xd, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d,
+                                             self.taps_d, cfg.zoom_n_fft, out=o["zoom"]))]
+
+    def launches(self):
+        return 3
+
+    def e2e(self):
+        """End-to-end step through the C-ABI with pinned host buffers."""
+        import torch
+        s, ctx, cfg = self.spec, self.ctx, self.cfg
+        xh = torch.from_numpy(self.x).pin_memory()
+        hs = {k: torch.empty(v.shape, dtype=torch.complex64).pin_memory() for k, v in self.out.items()}
+        xn = xh.numpy()
+        hn = {k: v.numpy() for k, v in hs.items()}
+
+        def step():
+            s.spec_fft(ctx, xn, cfg.fs, cfg.n_fft, out=hn["fft"])
+            s.spec_czt(ctx, xn, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, out=hn["czt"])
+            s.spec_zoom(ctx, xn, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, self.taps_h, cfg.zoom_n_fft,
+                        out=hn["zoom"])
+
+        def check():
+            return max(float(np.abs(hn[k] - self.out[k].cpu().numpy()).max()) for k in hn)
+        h2d = 3 * self.x.nbytes + self.taps_h.nbytes
+        d2h = sum(v.numel() * 8 for v in self.out.values())
+        return step, check, h2d, d2h
+
+    def cpu_leg(self):
+        b, dt, ref = oracle_uniform(self.cfg, self.B)
+        errs = {}
+        for k, got in self.out.items():
+            g = got.cpu().numpy().astype(np.complex128)
+            errs[k] = float((np.linalg.norm(g - ref[k], axis=1) / np.linalg.norm(ref[k], axis=1)).max())
+        cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"the whole batch ({self.B} traces), all bins of FFT, CZT and Zoom FFT, FP64 numpy, "
+                         f"{dt:.1f} s"}
+        return cpu, errs, "max_rel_l2_all_traces"
+
+
+class Ragged:
+    """Workload 2: 10000 ragged traces, one graph launch per transform."""
+
+    def __init__(self, spec, ctx, dev, count=10000):
+        import torch
+        self.spec, self.ctx = spec, ctx
+        rg = synth.ragged_params(count)
+        self.items = rg.items
+        self.traces = [synth.ragged_trace(i, it) for i, it in enumerate(self.items)]
+        xo = np.concatenate([[0], np.cumsum([len(t) for t in self.traces])[:-1]]).astype(np.int64)
+        self.x = np.concatenate(self.traces)
+        self.xd = torch.from_numpy(self.x).to(dev)
+        taps, to, toff = [], [], 0
+        for it in self.items:
+            taps.append(spec.spec_design_lowpass(it.n_taps, it.d))
+            to.append(toff)
+            toff += it.n_taps
+        self.taps_h = np.concatenate(taps)
+        self.taps_d = torch.from_numpy(self.taps_h).to(dev)
+        self.bins, self.bytes, self.flops, self.descs, self.offs, self.out = {}, {}, {}, {}, {}, {}
+        for kind, name in ((spec.SPEC_KIND_FFT, "fft"), (spec.SPEC_KIND_CZT, "czt"), (spec.SPEC_KIND_ZOOM, "zoom")):
+            cost = [trace_cost(name, it.n, it.n_fft, it.m, it.d, it.n_taps) for it in self.items]
+            nb = np.array([c[0] for c in cost], dtype=np.int64)
+            oo = np.concatenate([[0], np.cumsum(nb)[:-1]]).astype(np.int64)
+            self.bins[name] = int(nb.sum())
+            self.bytes[name] = float(sum(c[1] for c in cost))
+            self.flops[name] = float(sum(c[2] for c in cost))
+            self.offs[name] = (oo, nb)
+            self.descs[name] = (kind, [spec.spec_desc(int(xo[i]), it.n, int(oo[i]), it.f1, it.f2, it.n_fft, it.m,
+                                                      it.d, int(to[i]), it.n_taps) for i, it in enumerate(self.items)])
+            self.out[name] = torch.empty(int(nb.sum()), dtype=torch.complex64, device=dev)
+        self.name = W2_NAME
+
+    def parts(self):
+        s, ctx = self.spec, self.ctx
+
+        def call(name):
+            kind, d = self.descs[name]
+            return lambda: s.spec_ragged(ctx, kind, d, synth.FS, self.xd, self.out[name], self.taps_d)
+        return [(k, call(k)) for k in ("fft", "czt", "zoom")]
+
+    def launches(self):
+        return sum(self.spec.spec_ragged_launches(self.ctx, kind, d, synth.FS) for kind, d in self.descs.values())
+
+    def e2e(self):
+        """End-to-end step: pinned host pools copied in, the three ragged
+        calls, spectra copied out (the ragged API takes device pools)."""
+        import torch
+        xh = torch.from_numpy(self.x).pin_memory()
+        th = torch.from_numpy(self.taps_h).pin_memory()
+        hs = {k: torch.empty(v.shape, dtype=torch.complex64).pin_memory() for k, v in self.out.items()}
+        parts = self.parts()
+
+        def step():
+            self.xd.copy_(xh, non_blocking=True)
+            self.taps_d.copy_(th, non_blocking=True)
+            for _, f in parts:
+                f()
+            for k, v in self.out.items():
+                hs[k].copy_(v, non_blocking=True)
+
+        def check():
+            torch.cuda.synchronize()
+            return max(float((hs[k] - v.cpu()).abs().max()) for k, v in self.out.items())
+        h2d = self.x.nbytes + self.taps_h.nbytes
+        d2h = sum(v.numel() * 8 for v in self.out.values())
+        return step, check, h2d, d2h
+
+    def cpu_leg(self):
+        pick = list(range(0, len(self.items), max(1, len(self.items) // 8)))
+        b, dt, ref = oracle_ragged(self.items, self.traces, pick)
+        errs = {}
+        for k in ("fft", "czt", "zoom"):
+            oo, nb = self.offs[k]
+            got = self.out[k].cpu().numpy().astype(np.complex128)
+            errs[k] = max(float(np.linalg.norm(got[oo[i]:oo[i] + nb[i]] - ref[k][i]) / np.linalg.norm(ref[k][i]))
+                          for i in pick)
+        cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{len(pick)} of {len(self.items)} ragged traces, all bins of the three transforms, "
+                         f"FP64 numpy, {dt:.1f} s"}
+        return cpu, errs, "max_rel_l2_sampled_traces"
+
+
+# ---------------------------------------------------------------- our arm --
 
 def run_ours(args):
     import torch
@@ -207,30 +488,11 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = synth.UNIFORM[WORKLOAD]
-    B = cfg.batch
-    sizes = workload_sizes(cfg)
-    x = synth.batch_traces(WORKLOAD, range(B))
-    xd = torch.from_numpy(x).to(dev)
-    taps_h = spec.spec_design_lowpass(cfg.zoom_taps, cfg.zoom_d)
-    taps_d = torch.from_numpy(taps_h).to(dev)
-    X = torch.empty((B, sizes["fft"]["bins"]), dtype=torch.complex64, device=dev)
-    Z = torch.empty((B, sizes["czt"]["bins"]), dtype=torch.complex64, device=dev)
-    U = torch.empty((B, sizes["zoom"]["bins"]), dtype=torch.complex64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ctx = spec.Context(local)
+    W = Ragged(spec, ctx, dev) if args.workload == 2 else Uniform(spec, ctx, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def fft():
-        spec.spec_fft(ctx, xd, cfg.fs, cfg.n_fft, out=X)
-
-    def czt():
-        spec.spec_czt(ctx, xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, out=Z)
-
-    def zoom():
-        spec.spec_zoom(ctx, xd, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, taps_d, cfg.zoom_n_fft, out=U)
-
-    parts = [("fft", fft), ("czt", czt), ("zoom", zoom)]
+    parts = W.parts()
     for _ in range(max(3, args.warmup)):
         for _, f in parts:
             f()
@@ -240,7 +502,7 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(args.steps)]
     out_dir = os.path.join(ROOT, "gpurun_out")
     if not os.path.isdir(out_dir):
         import tempfile
@@ -257,25 +519,15 @@ def run_ours(args):
                 evs[s][i + 1].record(stream)
         torch.cuda.synchronize()
         barrier()
-    launches = args.steps * len(parts)
     per = {name: [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]
            for i, (name, _) in enumerate(parts)}
     step_ms = [sum(per[name][s] for name, _ in parts) for s in range(args.steps)]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
-    bins_step = B * sum(v["bins"] for v in sizes.values())
+    bins_step = sum(W.bins.values())
     value = job_throughput(bins_step, args.steps, world, total_ms / 1e3)
+    launches = W.launches() * args.steps
 
-    # end to end through the C-ABI with host buffers (pinned), copies included
-    xh = torch.from_numpy(x).pin_memory()
-    Xh = torch.empty(X.shape, dtype=torch.complex64).pin_memory()
-    Zh = torch.empty(Z.shape, dtype=torch.complex64).pin_memory()
-    Uh = torch.empty(U.shape, dtype=torch.complex64).pin_memory()
-    xn, Xn, Zn, Un = xh.numpy(), Xh.numpy(), Zh.numpy(), Uh.numpy()
-
-    def e2e_step():
-        spec.spec_fft(ctx, xn, cfg.fs, cfg.n_fft, out=Xn)
-        spec.spec_czt(ctx, xn, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, out=Zn)
-        spec.spec_zoom(ctx, xn, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, taps_h, cfg.zoom_n_fft, out=Un)
+    e2e_step, e2e_check, h2d, d2h = W.e2e()
     e2e_step()
     torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 10))
@@ -286,10 +538,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_val = job_throughput(bins_step, e2e_steps, world, e2e_s)
-    h2d = 3 * x.nbytes + taps_h.nbytes
-    d2h = X.numel() * 8 + Z.numel() * 8 + U.numel() * 8
-    e2e_parity = max(float(np.abs(Xn - X.cpu().numpy()).max()), float(np.abs(Zn - Z.cpu().numpy()).max()),
-                     float(np.abs(Un - U.cpu().numpy()).max()))
+    e2e_diff = e2e_check()
 
     if rank != 0:
         ctx.close()
@@ -299,13 +548,12 @@ def run_ours(args):
 
     hbm, hbm_kind = measured_peaks()
     kern = {}
-    for name in ("fft", "czt", "zoom"):
-        ms = statistics.mean(per[name])
-        gbs = B * sizes[name]["bytes"] / (ms / 1e3) / 1e9
-        tfl = B * sizes[name]["flops"] / (ms / 1e3) / 1e12
-        kern[name] = {"ms": ms, "bins_per_s": B * sizes[name]["bins"] / (ms / 1e3),
-                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm, "fp32_tflops": tfl,
-                      "fp32_frac": tfl / FP32_PEAK_TFLOPS}
+    for name, _ in parts:
+        ms = statistics.median(per[name])
+        gbs = W.bytes[name] / (ms / 1e3) / 1e9
+        tfl = W.flops[name] / (ms / 1e3) / 1e12
+        kern[name] = {"ms": ms, "bins_per_s": W.bins[name] / (ms / 1e3), "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
+                      "fp32_tflops": tfl, "fp32_frac": tfl / FP32_PEAK_TFLOPS}
     dom = max(kern, key=lambda k: kern[k]["ms"])
     if kern[dom]["hbm_frac"] >= kern[dom]["fp32_frac"]:
         roof = {"bound": "hbm", "achieved": kern[dom]["hbm_gbs"], "peak": hbm, "unit": "GB/s",
@@ -316,40 +564,32 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": kern[dom]["fp32_frac"], "traffic": None, "kernel": dom,
                 "peak_source": "FP32 FMA 152 SM x 128 x 2 x 2.07 GHz"}
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file):
+    if os.path.exists(traffic_file) and args.workload == 1:
         with open(traffic_file) as f:
             tr = json.load(f).get(dom)
         if tr and tr.get("per_launch_bytes"):
             roof["traffic"] = tr["per_launch_bytes"]
 
-    # CPU baseline leg (rank 0, N = 1 only): the FP64 oracle on the whole
-    # batch, timed; its outputs also give the parity of the timed GPU outputs.
+    # CPU-baseline leg (rank 0, N = 1 only): the FP64 oracle, timed; its
+    # outputs also give the parity of the timed GPU outputs.
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        b, dt, ref = oracle_sample(cfg, B)
-        cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"the whole batch ({B} traces), all bins of FFT, CZT and Zoom FFT, FP64 numpy, "
-                         f"{dt:.1f} s"}
-        for name, got in (("fft", X), ("czt", Z), ("zoom", U)):
-            g = got.cpu().numpy().astype(np.complex128)
-            r = ref[name]
-            err = np.linalg.norm(g - r, axis=1) / np.linalg.norm(r, axis=1)
-            kern[name]["max_rel_l2_all_traces"] = float(err.max())
+        cpu, errs, key = W.cpu_leg()
+        for k, v in errs.items():
+            kern[k][key] = v
 
     line = {
         "metric": METRIC, "value": value, "unit": "bins/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "4096 THz traces, N=2048 float32, fs=20 THz; FFT to 16384, CZT 0.2-2.5 THz "
-                               "M=1024, Zoom 1.35 THz D=4 63-tap Hamming; one launch per transform",
-                   "batch_per_gpu": B, "l2": "flushed before every step (256 MB write)",
+        "config": {"workload": W.name, "l2": "flushed before every step (256 MB write)",
                    "bins_per_step_per_gpu": bins_step},
         "roofline": roof,
         "kernels": kern,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps, "max_abs_diff_vs_device_path": e2e_parity},
+                "steps": e2e_steps, "max_abs_diff_vs_device_path": e2e_diff},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
@@ -363,8 +603,9 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

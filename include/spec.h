@@ -206,6 +206,13 @@ typedef struct {
 SPEC_API spec_status spec_ragged(spec_ctx* ctx, int kind, const spec_desc* descs, int64_t count, double fs,
                                  const float* x_pool, const float* taps_pool, float* X_pool, void* stream);
 
+/* Kernel launches one replay of the cached plan for these descriptors makes
+ * (one per class of traces, plus one FIR launch for Zoom FFTs too large for
+ * one CTA), or -1 if the context holds no such plan.  Library bookkeeping;
+ * the paper has no counterpart. */
+SPEC_API int64_t spec_ragged_launches(const spec_ctx* ctx, int kind, const spec_desc* descs, int64_t count,
+                                      double fs);
+
 /* ---- host-only helpers (pure functions, no CUDA calls) ----------------- */
 
 /* Zeros to append to an N_FFT-sample record so that its bin spacing shrinks

@@ -91,8 +91,11 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, F
     int n = a.n, m = a.m;
     const float2 *pre = a.pre, *V = a.V, *post = a.post;
     int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
-    if (a.items && live) {
-        const RaggedItem& it = a.items[b];
+    if (a.items) {
+        // a dead slot (b >= batch) borrows trace 0's tables so that the
+        // unguarded table reads below stay inside valid memory; its x loads
+        // and X stores remain switched off by `live`
+        const RaggedItem& it = a.items[live ? b : 0];
         xo = it.x_off;
         Xo = it.out_off;
         n = it.n;

@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(F
     // v[i] = Z[R q + r], q = t + T i.  Stage Z in natural order; CTA c of a
     // cluster owns Z[c chunk .. (c+1) chunk).
     const int chunk_mask = (1 << a.logChunk) - 1;
-    __syncthreads();
+    // Every CTA of a cluster must have finished its FFT (whose exchanges use
+    // this shared memory) before any of them writes Z into its peers.
+    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
     if (a.C == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
@@ -189,7 +191,9 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     FFT::run(v, s, t, a.tw);
 
     const int chunk_mask = (1 << a.logChunk) - 1;
-    __syncthreads();
+    // Every CTA of a cluster must have finished its FFT (whose exchanges use
+    // this shared memory) before any of them writes Z into its peers.
+    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
     if (a.C == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -302,7 +306,9 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
     FFT::run(v, s, t, a.tw);
 
     const int chunk = 1 << a.logChunk;
-    __syncthreads();
+    // Every CTA of a cluster must have finished its FFT (whose exchanges use
+    // this shared memory) before any of them writes Z into its peers.
+    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
     if (a.C == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];

@@ -402,3 +402,14 @@ extern "C" spec_status spec_ragged(spec_ctx* c, int kind, const spec_desc* descs
     if (e != cudaSuccess) return ctx_cuda_fail(c, e, "graph launch");
     return SPEC_OK;
 }
+
+// Kernel launches in one replay of the cached plan for these descriptors
+// (one per class, plus the FIR launch of the large Zoom path); -1 if the
+// context holds no such plan.
+extern "C" int64_t spec_ragged_launches(const spec_ctx* c, int kind, const spec_desc* descs, int64_t count,
+                                        double fs) {
+    if (!c || count < 0 || (count > 0 && !descs)) return -1;
+    for (const RaggedPlan* p : c->ragged)
+        if (same_descs(p, kind, fs, descs, count)) return (int64_t)p->classes.size() + (p->fir_count > 0 ? 1 : 0);
+    return -1;
+}

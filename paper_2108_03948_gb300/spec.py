@@ -26,7 +26,7 @@ _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "
            SPEC_EUNSUPPORTED: "SPEC_EUNSUPPORTED", SPEC_ETIMEOUT: "SPEC_ETIMEOUT"}
 
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
-           "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static", "spec_ragged",
+           "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static", "spec_ragged", "spec_ragged_launches",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
 
 SPEC_KIND_FFT, SPEC_KIND_CZT, SPEC_KIND_ZOOM = 0, 1, 2
@@ -73,6 +73,8 @@ def lib():
     L.spec_zoom.restype = C.c_int
     L.spec_ragged.argtypes = [vp, C.c_int, C.POINTER(spec_desc), i64, dbl, fp, fp, fp, vp]
     L.spec_ragged.restype = C.c_int
+    L.spec_ragged_launches.argtypes = [vp, C.c_int, C.POINTER(spec_desc), i64, dbl]
+    L.spec_ragged_launches.restype = i64
     L.spec_czt_static.argtypes = [fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, vp]
     L.spec_czt_static.restype = C.c_int
     L.spec_zeros_for_delta.argtypes = [dbl, i64, dbl]
@@ -228,6 +230,19 @@ def spec_ragged(ctx: Context, kind: int, descs, fs: float, x_pool, X_pool, taps_
                                 taps_pool.data_ptr() if taps_pool is not None else None,
                                 X_pool.data_ptr(), st))
     return X_pool
+
+
+def _desc_array(descs):
+    n = len(descs)
+    arr = (spec_desc * max(1, n))()
+    for i, dsc in enumerate(descs):
+        arr[i] = dsc if isinstance(dsc, spec_desc) else spec_desc(**dsc)
+    return arr, n
+
+
+def spec_ragged_launches(ctx: Context, kind: int, descs, fs: float) -> int:
+    arr, n = _desc_array(descs)
+    return int(lib().spec_ragged_launches(ctx.handle, int(kind), arr, n, float(fs)))
 
 
 # ---------------------------------------------------------------- helpers ---

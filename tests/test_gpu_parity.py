@@ -193,3 +193,28 @@ def test_workload1_full_batch_sampled(ctx, S):
     assert torch.isfinite(torch.view_as_real(X)).all()
     assert torch.isfinite(torch.view_as_real(Z)).all()
     assert torch.isfinite(torch.view_as_real(U)).all()
+
+
+# ------------------------------------- many clusters resident at once ------
+
+@pytest.mark.parametrize("kind", ["fft65536", "fft32768", "zoom32768"])
+def test_cluster_paths_under_full_occupancy(ctx, S, kind):
+    # Transforms large enough to run on thread-block clusters stage their
+    # result through peer shared memory; with thousands of clusters in flight
+    # any missing cluster-wide barrier shows as corrupted rows.  The batch
+    # repeats 8 distinct traces, so every copy must equal its original bit for
+    # bit and the originals must match the oracle.
+    n = 8192 if kind != "fft32768" else 4096
+    base = traces(8, n, 77)
+    x = np.tile(base, (150, 1))
+    if kind.startswith("fft"):
+        n_fft = int(kind[3:])
+        got = S.spec_fft(ctx, dev(x), 20e12, n_fft).cpu().numpy()
+        ref = O.fft_padded(base, n_fft)
+    else:
+        h = O.design_lowpass(63, 2).astype(np.float32)
+        got = S.spec_zoom(ctx, dev(x), 20e12, 0.2e12, 3.0e12, 2, dev(h), 65536).cpu().numpy()
+        ref = O.zoom(base, 20e12, 0.2e12, 3.0e12, 2, h, 65536)
+    got = got.reshape(150, 8, -1)
+    assert (got == got[:1]).all()
+    assert rel_rows(got[0], ref).max() <= TOL

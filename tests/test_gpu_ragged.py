@@ -132,3 +132,18 @@ def test_ragged_rejects_bad_descriptors(S, ctx):
     xh = np.zeros(64, np.float32)
     st = lib.spec_ragged(ctx.handle, 0, bad, 1, FS, xh.ctypes.data, None, X.data_ptr(), None)
     assert st == S.SPEC_EINVAL
+
+
+def test_ragged_czt_odd_class_with_two_traces_per_cta(S, ctx):
+    # L = 2048 runs two traces per CTA; an odd count leaves a dead slot in the
+    # last CTA, which must read only valid tables and write nothing.
+    items = [synth.RaggedTrace(1000, 8192, 0.2e12 + 0.1e12 * i, 1.5e12, 300 + 7 * i, 2, 31) for i in range(3)]
+    traces = [synth.ragged_trace(i, it) for i, it in enumerate(items)]
+    descs, x_pool, X_pool, taps_pool, bins, taps = pools(items, traces, 1)
+    S.spec_ragged(ctx, 1, descs, FS, x_pool, X_pool, taps_pool)
+    torch.cuda.synchronize()
+    got = X_pool.cpu().numpy()
+    for i, it in enumerate(items):
+        o, nb = descs[i]["out_off"], bins[i]
+        r = oracle(1, it, traces[i], taps[i])
+        assert np.linalg.norm(got[o:o + nb] - r) / np.linalg.norm(r) <= TOL
