@@ -13,13 +13,16 @@
 
 struct CztEntry {
     spec::CztTables t;
+    bool multipass = false;              // multi-pass Bluestein (L above one CTA)
+    spec::LongPlan lp;
+    float2* tw2 = nullptr;               // its twiddle table (inside mem)
     void* mem = nullptr;
     cudaEvent_t ready = nullptr;
     uint64_t last_use = 0;
 };
 
 struct FftEntry {
-    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables
+    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables, 2: multi-pass twiddles (H = period log2)
     int H = 0, LZ = 0, emax = 16;
     float2* tab = nullptr;
 };

@@ -100,6 +100,14 @@ __device__ __forceinline__ float2 unit_fixed(uint64_t ph, bool negative) {
     return negative ? make_float2(re, -im) : make_float2(re, im);
 }
 
+// e^{sign j 2 pi ph/2^64} evaluated in float64 (table generation only).
+__device__ __forceinline__ float2 unit_fixed_f64(uint64_t ph, bool negative) {
+    const double cyc = (double)(int64_t)ph * 5.421010862427522e-20;   // * 2^-64
+    double s, c;
+    sincospi(2.0 * cyc, &s, &c);
+    return make_float2((float)c, negative ? (float)-s : (float)s);
+}
+
 // ------------------------------------------------- two-lane complex pairs --
 // C2 holds two independent complex numbers a and b as packed FP32 pairs:
 // re = (a.x, b.x), im = (a.y, b.y).  Every operation below is one packed

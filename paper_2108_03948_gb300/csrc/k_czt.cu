@@ -19,14 +19,6 @@
 
 namespace spec {
 
-// e^{sign j 2 pi ph/2^64} evaluated in float64 (table generation only).
-__device__ __forceinline__ float2 unit_fixed_f64(uint64_t ph, bool negative) {
-    const double cyc = (double)(int64_t)ph * 5.421010862427522e-20;   // * 2^-64
-    double s, c;
-    sincospi(2.0 * cyc, &s, &c);
-    return make_float2((float)c, negative ? (float)-s : (float)s);
-}
-
 __global__ void k_czt_pre_post(float2* pre, int n, float2* post, int m, uint64_t A, uint64_t Bh) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t ii = (uint64_t)i;
@@ -205,6 +197,12 @@ bool czt_supported(int64_t n, int64_t m, std::string* why) {
         return false;
     }
     return true;
+}
+
+cudaError_t czt_pre_post_launch(const CztTables& t, cudaStream_t st) {
+    const int cnt = std::max(t.n, t.m);
+    k_czt_pre_post<<<(cnt + 255) / 256, 256, 0, st>>>(t.pre, t.n, t.post, t.m, t.A, t.Bh);
+    return cudaGetLastError();
 }
 
 cudaError_t czt_build_tables(const CztTables& t, const float2* tw, cudaStream_t st) {

@@ -217,6 +217,42 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     return SPEC_OK;
 }
 
+// Twiddle table of the multi-pass transforms (period 2^logTw), cached.
+spec_status long_table(spec_ctx* c, const LongPlan& p, const float2** tab) {
+    for (auto& it : c->fft)
+        if (it.kind == 2 && it.H == p.logTw) {
+            *tab = it.tab;
+            return SPEC_OK;
+        }
+    FftEntry ne;
+    ne.kind = 2;
+    ne.H = p.logTw;
+    std::vector<float2> host((size_t)long_fft_table_entries(p));
+    long_fill_tw(p, host.data());
+    cudaError_t e = cudaMalloc(&ne.tab, host.size() * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(ne.tab, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (ne.tab) cudaFree(ne.tab);
+        return cuda_fail(c, e, "multi-pass twiddles");
+    }
+    c->fft.push_back(ne);
+    *tab = ne.tab;
+    return SPEC_OK;
+}
+
+// Workspace of the multi-pass transforms: whole traces, at most ~1 GiB and
+// 65535 traces per chunk.
+spec_status long_work(spec_ctx* c, const LongPlan& p, int64_t batch, float2** work, int64_t* traces) {
+    const int64_t per = p.work_per_trace * (int64_t)sizeof(float2);
+    int64_t t = std::max<int64_t>(1, (int64_t(1) << 30) / per);
+    t = std::min<int64_t>({t, batch, 65535});
+    spec_status s = ensure_stage(c, 3, (size_t)(t * per));
+    if (s != SPEC_OK) return s;
+    *work = (float2*)c->stage[3];
+    *traces = t;
+    return SPEC_OK;
+}
+
 }  // namespace
 
 namespace spec {
@@ -320,14 +356,27 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if (s != SPEC_OK) return s;
     if (n_fft < n) return fail(c, SPEC_EINVAL, "n_fft must be >= n (padding never truncates)");
     FftPlan p;
-    std::string why;
-    if (!fft_plan(batch, n, n_fft, &p, &why)) return fail(c, SPEC_EUNSUPPORTED, why);
+    LongPlan lp;
+    std::string why, why_long;
+    const bool one_pass = fft_plan(batch, n, n_fft, &p, &why);
+    if (!one_pass && !long_fft_plan(n, n_fft, &lp, &why_long))
+        return fail(c, SPEC_EUNSUPPORTED, why + "; " + why_long);
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, bins, ld_X, &io)) != SPEC_OK) return s;
+    if (!one_pass) {
+        const float2* tw = nullptr;
+        float2* work = nullptr;
+        int64_t wt = 0;
+        if ((s = long_table(c, lp, &tw)) != SPEC_OK) return s;
+        if ((s = long_work(c, lp, batch, &work, &wt)) != SPEC_OK) return s;
+        cudaError_t e = long_fft_launch(lp, io.x, batch, (int)n, ld_x, c->block_tw, tw, work, wt, io.X, ld_X, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft multi-pass launch");
+        return stage_out_finish(c, X, batch, bins, ld_X, st, io);
+    }
     const float2* tab = nullptr;
     if (p.H > 0 && (s = plan_table(c, 0, p, &tab)) != SPEC_OK) return s;
     cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ, p.emax), tab,
@@ -344,8 +393,10 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if (s != SPEC_OK) return s;
     if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
     if (mode != SPEC_CZT_AUTO && mode != SPEC_CZT_BLUESTEIN) return fail(c, SPEC_EINVAL, "unknown CZT mode");
-    std::string why;
-    if (!czt_supported(n, m, &why)) return fail(c, SPEC_EUNSUPPORTED, why);
+    std::string why, why_long;
+    LongPlan lp;
+    const bool one_pass = czt_supported(n, m, &why);
+    if (!one_pass && !long_czt_plan(n, m, &lp, &why_long)) return fail(c, SPEC_EUNSUPPORTED, why + "; " + why_long);
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -354,7 +405,7 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     const double step = m > 1 ? (f2 - f1) / (double)(m - 1) : 0.0;
     const uint64_t A = cycles_to_fixed(f1 / fs);
     const uint64_t Bh = cycles_to_fixed(0.5 * (step / fs));
-    const int L = czt_length(n, m);
+    const int L = one_pass ? czt_length(n, m) : (1 << lp.logP);
     CztEntry* en = nullptr;
     for (auto& it : c->czt)
         if (it.t.n == n && it.t.m == m && it.t.L == L && it.t.A == A && it.t.Bh == Bh) en = &it;
@@ -369,15 +420,26 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         }
         CztEntry ne;
         ne.t.n = (int)n; ne.t.m = (int)m; ne.t.L = L; ne.t.A = A; ne.t.Bh = Bh;
-        const size_t elems = (size_t)n + (size_t)L + (size_t)m;
+        ne.multipass = !one_pass;
+        ne.lp = lp;
+        const size_t tw_elems = one_pass ? 0 : (size_t)long_czt_table_entries(lp);
+        const size_t elems = (size_t)n + (size_t)L + (size_t)m + tw_elems;
         cudaError_t e = cudaMalloc(&ne.mem, elems * sizeof(float2));
         if (e != cudaSuccess) return cuda_fail(c, e, "CZT tables");
         ne.t.pre = (float2*)ne.mem;
         ne.t.V = ne.t.pre + n;
         ne.t.post = ne.t.V + L;
+        if (!one_pass) {
+            ne.tw2 = ne.t.post + m;
+            std::vector<float2> host(tw_elems);
+            long_fill_tw(lp, host.data());
+            e = cudaMemcpy(ne.tw2, host.data(), tw_elems * sizeof(float2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { cudaFree(ne.mem); return cuda_fail(c, e, "CZT twiddles"); }
+        }
         e = cudaEventCreateWithFlags(&ne.ready, cudaEventDisableTiming);
         if (e != cudaSuccess) { cudaFree(ne.mem); return cuda_fail(c, e, "event"); }
-        e = czt_build_tables(ne.t, c->block_tw + block_twiddle_offset(L), st);
+        e = one_pass ? czt_build_tables(ne.t, c->block_tw + block_twiddle_offset(L), st)
+                     : long_czt_build_tables(lp, ne.t, c->block_tw, ne.tw2, st);
         if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
         if (e != cudaSuccess) {
             cudaFree(ne.mem);
@@ -395,6 +457,15 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
+    if (en->multipass) {
+        float2* work = nullptr;
+        int64_t wt = 0;
+        if ((s = long_work(c, en->lp, batch, &work, &wt)) != SPEC_OK) return s;
+        cudaError_t e = long_czt_launch(en->lp, en->t, en->tw2, io.x, batch, ld_x, c->block_tw, work, wt, io.X,
+                                        ld_X, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt multi-pass launch");
+        return stage_out_finish(c, X, batch, m, ld_X, st, io);
+    }
     cudaError_t e = (czt_dual_ok(L) && c->lanes != 1)
         ? czt_launch2(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st)
         : czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);

@@ -105,6 +105,36 @@ bool czt_dual_ok(int L);
 cudaError_t czt_launch2(const CztTables& t, const float* x, int64_t batch, int64_t ld_x,
                         const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
 
+cudaError_t czt_pre_post_launch(const CztTables& t, cudaStream_t st);
+
+// ---- multi-pass FFT and Bluestein (k_long.cu) ------------------------------
+// P = P1 x 512 points (P = N_FFT/2 for the padded FFT, L for Bluestein);
+// a column pass of pruned P1-point FFTs (LZ1 nonzero inputs, R1 = P1/LZ1
+// residues) and a row pass of 512-point FFTs through a workspace of P
+// complex values per trace.
+struct LongPlan {
+    int logP = 0, logP1 = 0, LZ1 = 0, logR1 = 0;
+    int logTw = 0;                   // period of the twiddle table (2P for the padded FFT)
+    int64_t work_per_trace = 0;      // float2
+};
+bool long_fft_plan(int64_t n, int64_t n_fft, LongPlan* p, std::string* why);
+bool long_czt_plan(int64_t n, int64_t m, LongPlan* p, std::string* why);
+int long_fft_table_entries(const LongPlan& p);
+int long_czt_table_entries(const LongPlan& p);
+void long_fill_tw(const LongPlan& p, float2* host);
+// work: work_traces x work_per_trace float2; the batch runs in chunks of
+// work_traces traces (<= 65535).
+cudaError_t long_fft_launch(const LongPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
+                            const float2* block_tw_base, const float2* tw_tab, float2* work, int64_t work_traces,
+                            float2* X, int64_t ld_X, cudaStream_t st);
+// Tables: t.pre (N), t.V (L, in the [k1][k2] order of the row pass, scaled
+// 1/L), t.post (M) and tw_tab (long_czt_table_entries, filled by the host).
+cudaError_t long_czt_build_tables(const LongPlan& p, const CztTables& t, const float2* block_tw_base,
+                                  float2* tw_tab, cudaStream_t st);
+cudaError_t long_czt_launch(const LongPlan& p, const CztTables& t, const float2* tw_tab, const float* x,
+                            int64_t batch, int64_t ld_x, const float2* block_tw_base, float2* work,
+                            int64_t work_traces, float2* X, int64_t ld_X, cudaStream_t st);
+
 // ---- Zoom FFT (k_zoom.cu) -------------------------------------------------
 struct ZoomPlan {
     int n = 0, d = 0, n_taps = 0, K = 0, lout = 0;
