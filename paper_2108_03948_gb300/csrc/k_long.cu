@@ -76,6 +76,13 @@ static Tw2 tw2_view(const float2* tab, int logP) {
     return t;
 }
 
+// Shared-memory stride between the column FFTs of a CTA.  A warp holds the
+// same element of 32 different columns, so the stride is made 1 modulo 16
+// (in 8-byte words): the warp's accesses then spread over all banks.
+__host__ __device__ constexpr int col_stride(int LF) {
+    return padded_len(LF) + (17 - padded_len(LF) % 16) % 16;
+}
+
 // ------------------------------------------------------------ column pass --
 enum ColInput : int {
     kPairs = 0,      // z[m] = x[2m] + j x[2m+1] (padded real FFT)
@@ -101,7 +108,7 @@ struct ColArgs {
 };
 
 template <int LZ1>
-__global__ void __launch_bounds__(512) k_long_cols(ColArgs a) {
+__global__ void __launch_bounds__(512, LZ1 >= 512 ? 1 : 2) k_long_cols(ColArgs a) {
     using FFT = BlockFFT<LZ1, false>;
     constexpr int E = FFT::E, T = FFT::T;
     extern __shared__ float2 smem[];
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(512) k_long_cols(ColArgs a) {
     const int P1 = 1 << a.logP1;
     const int up = a.tw.logP - a.logP;               // table index scale for w_P
     const int up1 = a.tw.logP - a.logP1;             // ... and for w_P1
-    float2* s = smem + c * padded_len(LZ1);
+    float2* s = smem + c * col_stride(LZ1);
 
     float2 v[E];
 #pragma unroll
@@ -166,7 +173,7 @@ struct RowRealArgs {
     const float2* btw;               // BlockFFT<kRow> twiddles
 };
 
-__global__ void __launch_bounds__(2 * kRowsPerCta * kRow / 16) k_long_rows_real(RowRealArgs a) {
+__global__ void __launch_bounds__(2 * kRowsPerCta * kRow / 16, 2) k_long_rows_real(RowRealArgs a) {
     using FFT = BlockFFT<kRow, false>;
     constexpr int E = FFT::E, T = FFT::T;
     constexpr int G = kRowsPerCta;
@@ -236,7 +243,7 @@ struct RowC2cArgs {
 // MODE 0: Bluestein row step (forward FFT, x V, inverse FFT, x w_P^{-k1 n2});
 // MODE 1: forward row FFT only (builds V in [k1][k2] order).
 template <int MODE>
-__global__ void __launch_bounds__(kRowsPerCta * kRow / 16) k_long_rows_c2c(RowC2cArgs a) {
+__global__ void __launch_bounds__(kRowsPerCta * kRow / 16, 4) k_long_rows_c2c(RowC2cArgs a) {
     using Fw = BlockFFT<kRow, false>;
     using Iv = BlockFFT<kRow, true>;
     constexpr int E = Fw::E, T = Fw::T;
@@ -283,7 +290,7 @@ struct ColInvArgs {
 };
 
 template <int P1>
-__global__ void __launch_bounds__(512) k_long_cols_inv(ColInvArgs a) {
+__global__ void __launch_bounds__(512, P1 >= 512 ? 1 : 2) k_long_cols_inv(ColInvArgs a) {
     using Iv = BlockFFT<P1, true>;
     constexpr int E = Iv::E, T = Iv::T;
     extern __shared__ float2 smem[];
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(512) k_long_cols_inv(ColInvArgs a) {
     const int t = threadIdx.x / a.G;
     const int n2 = blockIdx.x * a.G + c;
     const int64_t b = blockIdx.y;
-    float2* s = smem + c * padded_len(P1);
+    float2* s = smem + c * col_stride(P1);
     const float2* Wb = a.W + (b << a.logP);
     float2 v[E];
 #pragma unroll
@@ -353,7 +360,7 @@ static cudaError_t launch_cols(const LongPlan& p, ColArgs a, int64_t batch, cuda
     if (!k) return cudaErrorInvalidValue;
     const int G = cols_per_cta(p.LZ1);
     a.G = G;
-    const size_t smem = (size_t)G * padded_len(p.LZ1) * sizeof(float2);
+    const size_t smem = (size_t)G * col_stride(p.LZ1) * sizeof(float2);
     cudaError_t e = set_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
     const int T = std::max(1, p.LZ1 / 16);
@@ -487,7 +494,7 @@ cudaError_t long_czt_launch(const LongPlan& p, const CztTables& t, const float2*
     ColInvKernel ki = colinv_kernel_for(P1);
     if (!ki) return cudaErrorInvalidValue;
     const int Gi = cols_per_cta(P1);
-    const size_t smem_i = (size_t)Gi * padded_len(P1) * sizeof(float2);
+    const size_t smem_i = (size_t)Gi * col_stride(P1) * sizeof(float2);
     cudaError_t e = set_smem((const void*)ki, smem_i);
     if (e != cudaSuccess) return e;
     const int live_cols = (int)std::min<int64_t>(kRow, t.m);
