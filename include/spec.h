@@ -47,13 +47,25 @@ typedef enum {
 } spec_status;
 
 /* How spec_czt evaluates the chirp-z transform.
- *   SPEC_CZT_AUTO       the library picks (Bluestein unless a GEMM form is
- *                       faster at the 1e-5 accuracy bar).
- *   SPEC_CZT_BLUESTEIN  FP32 Bluestein: chirp, FFT convolution, chirp
- *                       (Section 2.3, Eq. 13-15).                         */
+ *   SPEC_CZT_AUTO          the library picks (Bluestein unless a GEMM form is
+ *                          faster at the 1e-5 accuracy bar).
+ *   SPEC_CZT_BLUESTEIN     FP32 Bluestein: chirp, FFT convolution, chirp
+ *                          (Section 2.3, Eq. 13-15).
+ *   SPEC_CZT_GEMM_F16X3    Eq. 11 as the product x Z^T, Z[k][n] = z_k^{-n},
+ *                          on the tensor cores: x (per-row power-of-two
+ *                          scale) and Z each split into two FP16 parts, three
+ *                          products accumulated in FP32.  Relative error a
+ *                          few 1e-7, like the FP32 path.  The paper has no
+ *                          counterpart (it uses Bluestein only).
+ *   SPEC_CZT_GEMM_F16X1    the same with one FP16 product: relative error
+ *                          about 1e-3 (below the 1e-5 bar; for screening).
+ * The GEMM modes cache Z (2 x 2M x ceil64(N) FP16) per (N, M, f1/fs,
+ * step/fs) and use a workspace of 4 bytes per input sample.             */
 typedef enum {
     SPEC_CZT_AUTO = 0,
-    SPEC_CZT_BLUESTEIN = 1
+    SPEC_CZT_BLUESTEIN = 1,
+    SPEC_CZT_GEMM_F16X3 = 2,
+    SPEC_CZT_GEMM_F16X1 = 3
 } spec_czt_mode;
 
 typedef struct spec_ctx spec_ctx;
@@ -74,8 +86,17 @@ SPEC_API void spec_ctx_destroy(spec_ctx* ctx);
 SPEC_API const char* spec_last_error(const spec_ctx* ctx);
 
 /* Wait for `stream` and report any deferred device-side error: SPEC_ECUDA
- * for a CUDA error, SPEC_ETIMEOUT if a bounded device wait gave up. */
+ * for a CUDA error, SPEC_ETIMEOUT if a bounded device wait gave up (the
+ * tensor-core kernels bound every wait on their pipeline barriers; a wait
+ * that gives up leaves that call's output incomplete).  Reading the status
+ * clears it. */
 SPEC_API spec_status spec_ctx_check(spec_ctx* ctx, void* stream);
+
+/* Self-test of the bounded-wait machinery: launches one CTA that waits on
+ * a barrier nothing will complete, with a limit of `timeout_us`
+ * microseconds (1 .. 10^6).  The next spec_ctx_check on `stream` must then
+ * return SPEC_ETIMEOUT.  No counterpart in the paper. */
+SPEC_API spec_status spec_selftest_wait_timeout(spec_ctx* ctx, int64_t timeout_us, void* stream);
 
 /*
  * Zero-padded FFT of real traces (Section 2.1, Eq. 2 with the forward sign

@@ -27,6 +27,14 @@ struct FftEntry {
     float2* tab = nullptr;
 };
 
+struct GemmZEntry {       // cached FP16 split of Z for the GEMM chirp-z
+    int64_t n = 0, m = 0;
+    uint64_t A = 0, B = 0;
+    void* z = nullptr;
+    cudaEvent_t ready = nullptr;
+    uint64_t last_use = 0;
+};
+
 struct RaggedPlan;       // ragged.cu
 void ragged_plan_free(RaggedPlan* p);
 
@@ -37,6 +45,10 @@ struct spec_ctx {
     int lanes = 1;                       // 1: one FFT per thread group; 2: two packed lanes where possible
     std::vector<FftEntry> fft;
     std::vector<CztEntry> czt;
+    std::vector<GemmZEntry> gemm_z;
+    unsigned* status = nullptr;          // device word: bit 0 = a bounded wait gave up
+    int sms = 0;                         // multiprocessors (persistent grids)
+    uint64_t wait_timeout_ns = 1000000000ull;
     std::vector<RaggedPlan*> ragged;     // cached ragged-batch plans (graph + per-trace tables)
     uint64_t tick = 0;
     void* stage[4] = {nullptr, nullptr, nullptr, nullptr};   // x, X, taps, workspace

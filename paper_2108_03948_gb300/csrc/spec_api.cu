@@ -217,6 +217,67 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     return SPEC_OK;
 }
 
+// Chirp-z as the tensor-core product x Z^T (k_gemm.cu): Z cached per
+// (N, M, f1/fs, step/fs), the batch run in chunks whose FP16 split fits a
+// ~1 GiB workspace.
+spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs, double f1,
+                     double f2, int64_t m, int terms, float* X, int64_t ld_X, cudaStream_t st) {
+    if (gemm_z_bytes(n, m) > (size_t(1) << 31))
+        return fail(c, SPEC_EUNSUPPORTED, "GEMM chirp-z: Z above 2 GiB (use SPEC_CZT_BLUESTEIN)");
+    if (batch == 0) return SPEC_OK;
+    DeviceGuard g(c->device);
+    const double step = m > 1 ? (f2 - f1) / (double)(m - 1) : 0.0;
+    const uint64_t A = cycles_to_fixed(f1 / fs);
+    const uint64_t B = cycles_to_fixed(step / fs);
+    GemmZEntry* en = nullptr;
+    for (auto& it : c->gemm_z)
+        if (it.n == n && it.m == m && it.A == A && it.B == B) en = &it;
+    if (!en) {
+        if (c->gemm_z.size() >= kCztCacheMax) {
+            auto lru = std::min_element(c->gemm_z.begin(), c->gemm_z.end(),
+                                        [](const GemmZEntry& a, const GemmZEntry& b) { return a.last_use < b.last_use; });
+            cudaDeviceSynchronize();
+            cudaFree(lru->z);
+            cudaEventDestroy(lru->ready);
+            c->gemm_z.erase(lru);
+        }
+        GemmZEntry ne;
+        ne.n = n; ne.m = m; ne.A = A; ne.B = B;
+        cudaError_t e = cudaMalloc(&ne.z, gemm_z_bytes(n, m));
+        if (e != cudaSuccess) return cuda_fail(c, e, "GEMM Z table");
+        e = cudaEventCreateWithFlags(&ne.ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) { cudaFree(ne.z); return cuda_fail(c, e, "event"); }
+        e = gemm_build_z(n, m, A, B, ne.z, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
+        if (e != cudaSuccess) {
+            cudaFree(ne.z);
+            cudaEventDestroy(ne.ready);
+            return cuda_fail(c, e, "GEMM Z build");
+        }
+        c->gemm_z.push_back(ne);
+        en = &c->gemm_z.back();
+    } else {
+        cudaError_t e = cudaStreamWaitEvent(st, en->ready, 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "table wait");
+    }
+    en->last_use = ++c->tick;
+    Io io;
+    spec_status s;
+    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
+    if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
+    const int64_t per_row = (int64_t)gemm_padded_n(n) * 4 + 4;
+    int64_t chunk = std::max<int64_t>(128, ((int64_t(1) << 30) / per_row) / 128 * 128);
+    chunk = std::min(chunk, batch);
+    if ((s = ensure_stage(c, 3, gemm_work_bytes(chunk, n))) != SPEC_OK) return s;
+    for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
+        const int64_t nb = std::min(chunk, batch - b0);
+        cudaError_t e = gemm_czt_launch(io.x + b0 * ld_x, nb, n, ld_x, m, terms, en->z, c->stage[3], io.X + b0 * ld_X,
+                                        ld_X, c->status, c->sms, c->wait_timeout_ns, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "GEMM chirp-z launch");
+    }
+    return stage_out_finish(c, X, batch, m, ld_X, st, io);
+}
+
 // Twiddle table of the multi-pass transforms (period 2^logTw), cached.
 spec_status long_table(spec_ctx* c, const LongPlan& p, const float2** tab) {
     for (auto& it : c->fft)
@@ -311,6 +372,21 @@ spec_status spec_ctx_create(spec_ctx** ctx, int device) {
             return e == cudaErrorMemoryAllocation ? SPEC_ENOMEM : SPEC_ECUDA;
         }
     }
+    e = cudaMalloc(&c->status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("status word: ") + cudaGetErrorString(e);
+        if (c->status) cudaFree(c->status);
+        cudaFree(c->block_tw);
+        delete c;
+        return SPEC_ECUDA;
+    }
+    if (const char* ev = std::getenv("SPEC_WAIT_TIMEOUT_MS")) {
+        const long long ms = std::atoll(ev);
+        if (ms > 0) c->wait_timeout_ns = (uint64_t)ms * 1000000ull;
+    }
     *ctx = c;
     return SPEC_OK;
 }
@@ -326,6 +402,11 @@ void spec_ctx_destroy(spec_ctx* c) {
         }
         for (auto& en : c->fft)
             if (en.tab) cudaFree(en.tab);
+        for (auto& en : c->gemm_z) {
+            if (en.z) cudaFree(en.z);
+            if (en.ready) cudaEventDestroy(en.ready);
+        }
+        if (c->status) cudaFree(c->status);
         for (RaggedPlan* rp : c->ragged) ragged_plan_free(rp);
         if (c->block_tw) cudaFree(c->block_tw);
         for (int i = 0; i < 4; ++i)
@@ -342,7 +423,24 @@ spec_status spec_ctx_check(spec_ctx* c, void* stream) {
     DeviceGuard g(c->device);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    unsigned word = 0;
+    e = cudaMemcpy(&word, c->status, sizeof(word), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status word");
+    if (word != 0) {
+        e = cudaMemset(c->status, 0, sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(c, e, "status word");
+        return fail(c, SPEC_ETIMEOUT, "a bounded device-side wait gave up; the output of that call is incomplete");
+    }
     c->err.clear();
+    return SPEC_OK;
+}
+
+spec_status spec_selftest_wait_timeout(spec_ctx* c, int64_t timeout_us, void* stream) {
+    if (!c) return SPEC_EINVAL;
+    if (timeout_us < 1 || timeout_us > 1000000) return fail(c, SPEC_EINVAL, "timeout_us must be in [1, 10^6]");
+    DeviceGuard g(c->device);
+    cudaError_t e = wait_selftest_launch(c->status, (uint64_t)timeout_us * 1000ull, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "self-test launch");
     return SPEC_OK;
 }
 
@@ -392,7 +490,10 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     spec_status s = check_common(c, x, batch, n, ld_x, fs, X, m, ld_X);
     if (s != SPEC_OK) return s;
     if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
-    if (mode != SPEC_CZT_AUTO && mode != SPEC_CZT_BLUESTEIN) return fail(c, SPEC_EINVAL, "unknown CZT mode");
+    if (mode < SPEC_CZT_AUTO || mode > SPEC_CZT_GEMM_F16X1) return fail(c, SPEC_EINVAL, "unknown CZT mode");
+    if (mode == SPEC_CZT_GEMM_F16X3 || mode == SPEC_CZT_GEMM_F16X1)
+        return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, mode == SPEC_CZT_GEMM_F16X3 ? 3 : 1, X, ld_X,
+                        (cudaStream_t)stream);
     std::string why, why_long;
     LongPlan lp;
     const bool one_pass = czt_supported(n, m, &why);

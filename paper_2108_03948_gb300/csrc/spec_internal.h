@@ -135,6 +135,17 @@ cudaError_t long_czt_launch(const LongPlan& p, const CztTables& t, const float2*
                             int64_t batch, int64_t ld_x, const float2* block_tw_base, float2* work,
                             int64_t work_traces, float2* X, int64_t ld_X, cudaStream_t st);
 
+// ---- chirp-z as a tensor-core product (k_gemm.cu) --------------------------
+int gemm_padded_n(int64_t n);
+size_t gemm_z_bytes(int64_t n, int64_t m);          // Zh | Zl, FP16 [2M][ceil64(N)] each
+size_t gemm_work_bytes(int64_t batch, int64_t n);   // xh | xl | row exponents
+cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, cudaStream_t st);
+// terms 3: split FP16 (FP32-level accuracy); 1: one FP16 product.
+cudaError_t gemm_czt_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int64_t m, int terms,
+                            const void* z, void* work, float2* X, int64_t ld_X, unsigned* status, int sms,
+                            uint64_t timeout_ns, cudaStream_t st);
+cudaError_t wait_selftest_launch(unsigned* status, uint64_t timeout_ns, cudaStream_t st);
+
 // ---- Zoom FFT (k_zoom.cu) -------------------------------------------------
 struct ZoomPlan {
     int n = 0, d = 0, n_taps = 0, K = 0, lout = 0;

@@ -20,12 +20,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libspec.so")
 
 SPEC_OK, SPEC_EINVAL, SPEC_ENOMEM, SPEC_ECUDA, SPEC_EUNSUPPORTED, SPEC_ETIMEOUT = range(6)
-SPEC_CZT_AUTO, SPEC_CZT_BLUESTEIN = 0, 1
+SPEC_CZT_AUTO, SPEC_CZT_BLUESTEIN, SPEC_CZT_GEMM_F16X3, SPEC_CZT_GEMM_F16X1 = 0, 1, 2, 3
 
 _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "SPEC_ECUDA",
            SPEC_EUNSUPPORTED: "SPEC_EUNSUPPORTED", SPEC_ETIMEOUT: "SPEC_ETIMEOUT"}
 
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
+           "spec_selftest_wait_timeout",
            "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static", "spec_ragged", "spec_ragged_launches",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
 
@@ -65,6 +66,8 @@ def lib():
     L.spec_last_error.restype = C.c_char_p
     L.spec_ctx_check.argtypes = [vp, vp]
     L.spec_ctx_check.restype = C.c_int
+    L.spec_selftest_wait_timeout.argtypes = [vp, i64, vp]
+    L.spec_selftest_wait_timeout.restype = C.c_int
     L.spec_fft.argtypes = [vp, fp, i64, i64, i64, dbl, i64, fp, i64, vp]
     L.spec_fft.restype = C.c_int
     L.spec_czt.argtypes = [vp, fp, i64, i64, i64, dbl, dbl, dbl, i64, C.c_int, fp, i64, vp]
@@ -261,3 +264,22 @@ def spec_design_lowpass(n_taps: int, d: int) -> np.ndarray:
     if st != SPEC_OK:
         raise SpecError(st, "invalid n_taps or d")
     return out
+
+
+# ------------------------------------------------------- status, self-test ---
+
+def _stream_handle(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def ctx_status(ctx: Context, stream=None) -> int:
+    """spec_ctx_check's raw status (SPEC_OK, SPEC_ETIMEOUT, ...) without raising."""
+    return lib().spec_ctx_check(ctx.handle, _stream_handle(stream))
+
+
+def spec_selftest_wait_timeout(ctx: Context, timeout_us: int, stream=None):
+    """Launch the bounded-wait self-test; the next ctx_status is SPEC_ETIMEOUT."""
+    ctx.check(lib().spec_selftest_wait_timeout(ctx.handle, int(timeout_us), _stream_handle(stream)))

@@ -1,0 +1,131 @@
+"""Chirp-z as a tensor-core product (SPEC_CZT_GEMM_F16X3 / _F16X1): parity
+with the FP64 oracle element by element, on shapes that leave ragged tiles
+in every dimension (traces not a multiple of 128, samples not a multiple of
+64, 2M not a multiple of 128), the degenerate M = 1 and descending bands,
+the full workload-3 batch in the bench's launch configuration (sampled
+traces), and the bounded-wait machinery."""
+import numpy as np
+import pytest
+
+from oracle import spec_oracle as O
+from paper_2108_03948_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+FS = synth.FS
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2108_03948_gb300 import build
+    build.build()
+    from paper_2108_03948_gb300 import spec
+    return spec
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    return np.linalg.norm(got - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+
+
+def noise(batch, n, seed):
+    return np.random.default_rng(seed).standard_normal((batch, n)).astype(np.float32)
+
+
+CASES = [
+    (300, 1024, 0.8e12, 1.2e12, 512),      # workload-3 shape
+    (129, 1000, 0.2e12, 2.5e12, 100),      # ragged in every dimension
+    (5, 37, 0.1e12, 9.0e12, 3),
+    (3, 2048, 0.2e12, 2.5e12, 1024),       # workload-1 shape
+    (4, 500, 1.3e12, 1.3e12, 1),           # M = 1
+    (7, 777, 3.0e12, 0.4e12, 257),         # descending band
+    (2, 4096, 0.0, 10.0e12, 2048),
+]
+
+
+@pytest.mark.parametrize("batch,n,f1,f2,m", CASES)
+def test_gemm_f16x3_parity(ctx, S, batch, n, f1, f2, m):
+    x = noise(batch, n, n + m)
+    got = S.spec_czt(ctx, dev(x), FS, f1, f2, m, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    assert got.shape == (batch, m)
+    assert rel(got, O.czt(x, FS, f1, f2, m)).max() <= TOL
+
+
+def test_gemm_f16x3_scale_invariance(ctx, S):
+    # per-row power-of-two scaling: rows of very different magnitude
+    x = noise(6, 1024, 1)
+    x *= np.array([1e-30, 1e-8, 1.0, 3e5, 1e20, 1e30], dtype=np.float32)[:, None]
+    got = S.spec_czt(ctx, dev(x), FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    assert rel(got, O.czt(x, FS, 0.8e12, 1.2e12, 512)).max() <= TOL
+
+
+def test_gemm_thz_traces(ctx, S):
+    cfg = synth.UNIFORM[3]
+    x = synth.batch_traces(3, range(200))
+    got = S.spec_czt(ctx, dev(x), cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, mode=S.SPEC_CZT_GEMM_F16X3)
+    ref = O.czt(x, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m)
+    assert rel(got.cpu().numpy(), ref).max() <= TOL
+
+
+def test_gemm_f16x1_is_the_low_precision_form(ctx, S):
+    x = noise(64, 1024, 2)
+    got = S.spec_czt(ctx, dev(x), FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X1).cpu().numpy()
+    err = rel(got, O.czt(x, FS, 0.8e12, 1.2e12, 512))
+    assert err.max() <= 3e-3
+    assert err.max() > 1e-6           # it really is the one-product form
+
+
+def test_gemm_matches_bluestein(ctx, S):
+    x = dev(noise(256, 1024, 3))
+    g = S.spec_czt(ctx, x, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    b = S.spec_czt(ctx, x, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_BLUESTEIN).cpu().numpy()
+    assert rel(g, b.astype(np.complex128)).max() <= 2e-6
+
+
+def test_gemm_host_buffers_and_repeat(ctx, S):
+    x = noise(130, 700, 4)
+    d = S.spec_czt(ctx, dev(x), FS, 0.5e12, 1.5e12, 300, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    d2 = S.spec_czt(ctx, dev(x), FS, 0.5e12, 1.5e12, 300, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    h = S.spec_czt(ctx, x, FS, 0.5e12, 1.5e12, 300, mode=S.SPEC_CZT_GEMM_F16X3)
+    assert np.array_equal(d, d2)
+    assert np.array_equal(np.asarray(h), d)
+
+
+def test_workload3_full_batch_sampled(ctx, S):
+    cfg = synth.UNIFORM[3]
+    idx = np.arange(cfg.batch)
+    x = synth.batch_traces(3, range(1024))
+    xall = np.tile(x, (cfg.batch // 1024, 1))         # 65536 traces, 64 copies of 1024 distinct ones
+    got = S.spec_czt(ctx, dev(xall), cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, mode=S.SPEC_CZT_GEMM_F16X3)
+    torch.cuda.synchronize()
+    assert S.ctx_status(ctx) == S.SPEC_OK
+    g = got.cpu().numpy()
+    assert np.isfinite(g).all()
+    pick = [0, 1, 127, 128, 1023]
+    ref = O.czt(x[pick], cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m)
+    for r in (0, 5, 63):                             # the same traces in different tiles give the same bits
+        assert rel(g[r * 1024 + np.array(pick)], ref).max() <= TOL
+    assert np.array_equal(g[idx[:1024]], g[idx[-1024:]])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(ctx, S):
+    assert S.ctx_status(ctx) == S.SPEC_OK
+    S.spec_selftest_wait_timeout(ctx, 2000)                 # a 2 ms wait on a barrier nothing completes
+    assert S.ctx_status(ctx) == S.SPEC_ETIMEOUT
+    assert S.ctx_status(ctx) == S.SPEC_OK                   # reading clears it
+    x = noise(2, 256, 9)
+    got = S.spec_czt(ctx, dev(x), FS, 0.5e12, 1.0e12, 64, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    assert rel(got, O.czt(x, FS, 0.5e12, 1.0e12, 64)).max() <= TOL
