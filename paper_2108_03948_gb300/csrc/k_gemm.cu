@@ -422,21 +422,28 @@ cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, 
     return cudaGetLastError();
 }
 
-cudaError_t gemm_czt_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int64_t m, int terms,
-                            const void* z, void* work, float2* X, int64_t ld_X, unsigned* status, int sms,
-                            uint64_t timeout_ns, cudaStream_t st) {
+cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int terms, void* work,
+                              cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
     const int np = gemm_padded_n(n);
     __half* xh = (__half*)work;
     __half* xl = xh + (size_t)batch * np;
     int* row_pow = (int*)((uint8_t*)work + ((size_t)2 * batch * np * sizeof(__half) + 255) / 256 * 256);
+    k_gemm_split_x<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>(x, batch, (int)n, ld_x, np, xh, xl, row_pow, terms);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, const void* z, const void* work,
+                            float2* X, int64_t ld_X, unsigned* status, int sms, uint64_t timeout_ns,
+                            cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    const int np = gemm_padded_n(n);
+    const __half* xh = (const __half*)work;
+    const __half* xl = xh + (size_t)batch * np;
+    const int* row_pow =
+        (const int*)((const uint8_t*)work + ((size_t)2 * batch * np * sizeof(__half) + 255) / 256 * 256);
     const __half* zh = (const __half*)z;
     const __half* zl = zh + (size_t)2 * m * np;
-
-    k_gemm_split_x<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>(x, batch, (int)n, ld_x, np, xh, xl, row_pow, terms);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-
     CUtensorMap mAh, mAl, mBh, mBl;
     if (!make_map(&mAh, xh, batch, np) || !make_map(&mAl, xl, batch, np) || !make_map(&mBh, zh, 2 * m, np) ||
         !make_map(&mBl, zl, 2 * m, np))
@@ -453,7 +460,7 @@ cudaError_t gemm_czt_launch(const float* x, int64_t batch, int64_t n, int64_t ld
     a.ld_out = 2 * ld_X;
     a.status = status;
     a.timeout_ns = timeout_ns;
-    e = cudaFuncSetAttribute(k_czt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_czt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.tiles, (int64_t)std::max(1, sms));
     k_czt_gemm<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a);

@@ -217,6 +217,21 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     return SPEC_OK;
 }
 
+// SPEC_CZT_AUTO: the split-FP16 GEMM when its modelled time per trace is
+// clearly below Bluestein's and the batch fills the GPU with tiles.  Model
+// (measured on GB300): GEMM 12 N M flop at 1.4 PFLOP/s plus 8 N bytes of
+// split traffic at 6 TB/s; Bluestein 0.39 ps x L log2 L (560 us for 65536
+// traces at L = 2048, 80 us for 4096 at L = 4096).
+bool auto_prefers_gemm(const spec_ctx* c, int64_t batch, int64_t n, int64_t m) {
+    if (gemm_z_bytes(n, m) > (size_t(1) << 31)) return false;
+    const int64_t tiles = (batch + 127) / 128 * ((2 * m + 127) / 128);
+    if (tiles < std::max(1, c->sms)) return false;
+    const double L = (double)next_pow2(std::max<int64_t>(16, n + m - 1));
+    const double t_gemm = 12.0 * (double)n * (double)m / 1.4e15 + 8.0 * (double)n / 6e12;
+    const double t_blue = 0.39e-12 * L * std::log2(L);
+    return t_gemm < 0.9 * t_blue;
+}
+
 // Chirp-z as the tensor-core product x Z^T (k_gemm.cu): Z cached per
 // (N, M, f1/fs, step/fs), the batch run in chunks whose FP16 split fits a
 // ~1 GiB workspace.
@@ -265,14 +280,20 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     spec_status s;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
+    // The FP16 split then the product, in chunks only when the workspace
+    // would exceed 512 MiB (one product over the whole batch keeps the tile
+    // waves full; smaller products measured slower, even with the split of
+    // the next chunk overlapped).
     const int64_t per_row = (int64_t)gemm_padded_n(n) * 4 + 4;
-    int64_t chunk = std::max<int64_t>(128, ((int64_t(1) << 30) / per_row) / 128 * 128);
+    int64_t chunk = std::max<int64_t>(128, ((int64_t(1) << 29) / per_row) / 128 * 128);
     chunk = std::min(chunk, batch);
     if ((s = ensure_stage(c, 3, gemm_work_bytes(chunk, n))) != SPEC_OK) return s;
     for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
         const int64_t nb = std::min(chunk, batch - b0);
-        cudaError_t e = gemm_czt_launch(io.x + b0 * ld_x, nb, n, ld_x, m, terms, en->z, c->stage[3], io.X + b0 * ld_X,
-                                        ld_X, c->status, c->sms, c->wait_timeout_ns, st);
+        cudaError_t e = gemm_split_launch(io.x + b0 * ld_x, nb, n, ld_x, terms, c->stage[3], st);
+        if (e == cudaSuccess)
+            e = gemm_mul_launch(nb, n, m, terms, en->z, c->stage[3], io.X + b0 * ld_X, ld_X, c->status, c->sms,
+                                c->wait_timeout_ns, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "GEMM chirp-z launch");
     }
     return stage_out_finish(c, X, batch, m, ld_X, st, io);
@@ -491,6 +512,7 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if (s != SPEC_OK) return s;
     if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
     if (mode < SPEC_CZT_AUTO || mode > SPEC_CZT_GEMM_F16X1) return fail(c, SPEC_EINVAL, "unknown CZT mode");
+    if (mode == SPEC_CZT_AUTO && auto_prefers_gemm(c, batch, n, m)) mode = SPEC_CZT_GEMM_F16X3;
     if (mode == SPEC_CZT_GEMM_F16X3 || mode == SPEC_CZT_GEMM_F16X1)
         return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, mode == SPEC_CZT_GEMM_F16X3 ? 3 : 1, X, ld_X,
                         (cudaStream_t)stream);

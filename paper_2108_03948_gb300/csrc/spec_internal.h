@@ -140,10 +140,14 @@ int gemm_padded_n(int64_t n);
 size_t gemm_z_bytes(int64_t n, int64_t m);          // Zh | Zl, FP16 [2M][ceil64(N)] each
 size_t gemm_work_bytes(int64_t batch, int64_t n);   // xh | xl | row exponents
 cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, cudaStream_t st);
-// terms 3: split FP16 (FP32-level accuracy); 1: one FP16 product.
-cudaError_t gemm_czt_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int64_t m, int terms,
-                            const void* z, void* work, float2* X, int64_t ld_X, unsigned* status, int sms,
-                            uint64_t timeout_ns, cudaStream_t st);
+// terms 3: split FP16 (FP32-level accuracy); 1: one FP16 product.  The
+// split writes x's FP16 parts and row exponents into `work`
+// (gemm_work_bytes(batch, n)); the product reads them.
+cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int terms, void* work,
+                              cudaStream_t st);
+cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, const void* z, const void* work,
+                            float2* X, int64_t ld_X, unsigned* status, int sms, uint64_t timeout_ns,
+                            cudaStream_t st);
 cudaError_t wait_selftest_launch(unsigned* status, uint64_t timeout_ns, cudaStream_t st);
 
 // ---- Zoom FFT (k_zoom.cu) -------------------------------------------------

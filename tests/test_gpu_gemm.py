@@ -129,3 +129,28 @@ def test_bounded_wait_reports_timeout_and_context_survives(ctx, S):
     x = noise(2, 256, 9)
     got = S.spec_czt(ctx, dev(x), FS, 0.5e12, 1.0e12, 64, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
     assert rel(got, O.czt(x, FS, 0.5e12, 1.0e12, 64)).max() <= TOL
+
+
+def test_auto_mode_choice(ctx, S):
+    # workload-3 shape: AUTO takes the split-FP16 GEMM; workload-1 shape: Bluestein
+    x3 = dev(np.tile(noise(1024, 1024, 5), (64, 1)))
+    a = S.spec_czt(ctx, x3, FS, 0.8e12, 1.2e12, 512)
+    g = S.spec_czt(ctx, x3, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3)
+    assert torch.equal(torch.view_as_real(a), torch.view_as_real(g))
+    x1 = dev(noise(4096, 2048, 6))
+    a = S.spec_czt(ctx, x1, FS, 0.2e12, 2.5e12, 1024)
+    b = S.spec_czt(ctx, x1, FS, 0.2e12, 2.5e12, 1024, mode=S.SPEC_CZT_BLUESTEIN)
+    assert torch.equal(torch.view_as_real(a), torch.view_as_real(b))
+
+
+def test_gemm_large_batch_matches_small_calls(ctx, S):
+    # many tiles per CTA of the persistent grid: every copy of a trace gives
+    # the same bits as a call with that trace block alone
+    x = noise(1024, 1024, 8)
+    xall = dev(np.tile(x, (48, 1)))                          # 49152 traces: 3 chunks
+    big = S.spec_czt(ctx, xall, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3)
+    one = S.spec_czt(ctx, dev(x), FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3)
+    torch.cuda.synchronize()
+    b = big.view(48, 1024, 512)
+    for r in (0, 17, 33, 47):
+        assert torch.equal(torch.view_as_real(b[r]), torch.view_as_real(one))
