@@ -45,6 +45,10 @@ METRIC = "spectral bins/s per transform at ≤1e-5 rel L2 vs FP64; % HBM/tensor 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 W1_NAME = ("4096 THz traces, N=2048 float32, fs=20 THz; FFT to 16384, CZT 0.2-2.5 THz M=1024, "
            "Zoom 1.35 THz D=4 63-tap Hamming; one launch per transform")
+W3_NAME = ("65536 THz traces, N=1024 float32, fs=20 THz; FFT to 8192, CZT 0.8-1.2 THz M=512 as a split-FP16 "
+           "tensor-core product, Zoom 1.0 THz D=4 63-tap Hamming; one launch sequence per transform")
+W4_NAME = ("256 THz traces, N=262144 float32 (pulse + 8 echoes), fs=20 THz; FFT to 2^21 (multi-pass), CZT "
+           "0.3-0.4 THz M=65536 (multi-pass Bluestein, L=2^19), Zoom 0.35 THz D=64 255-tap Hamming (K=32768)")
 W2_NAME = ("10000 ragged THz traces, N 1000-8192, fs=20 THz, N_FFT=8 nextpow2(N); per-trace CZT band "
            "(f1 0.1-1.0 THz, width 0.5-3.0 THz, M 256-4096) and Zoom (D 2-16, 31-127 taps); "
            "one CUDA-graph launch per transform")
@@ -81,6 +85,44 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_tensor_peak():
+    """Dense FP16 tensor peak: the measured bf16 cuBLAS burst figure (FP16 and
+    BF16 run at the same dense rate on this GPU)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured bf16_tflops burst (of measured; FP16 = BF16 dense rate)"
+    return 1900.0, "fallback 1.9 PFLOP/s bf16 burst (of fallback)"
+
+
+def csrc_digest():
+    """Digest of the kernel sources: stored traffic counters are valid only
+    for the sources they were taken from."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2108_03948_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when absent or taken from other sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"workload_{workload}", {}).get(kernel)
+    if not e or e.get("csrc_digest") != csrc_digest():
+        return None
+    return e.get("per_launch_bytes")
+
+
 def trace_cost(kind, n, n_fft=0, m=0, d=1, taps=1):
     """Bins, algorithmic bytes (input read once, output written once) and
     algorithmic flops of one trace."""
@@ -89,6 +131,9 @@ def trace_cost(kind, n, n_fft=0, m=0, d=1, taps=1):
     if kind == "czt":
         L = max(16, 1 << (n + m - 2).bit_length())
         return m, 4 * n + 8 * m, 2 * 5 * L * np.log2(L) + 6 * (n + L + m)
+    if kind == "czt_gemm":
+        # three FP16 products of [1 x N] . [N x 2M] per trace (tensor-core flops)
+        return m, 4 * n + 8 * m, 3 * 2 * n * 2 * m
     K = n_fft // d
     lout = (n + taps - 1 + d - 1) // d
     return K, 4 * n + 8 * K, 4 * lout * taps + 6 * n + 5 * K * np.log2(max(K, 2))
@@ -252,6 +297,28 @@ def oracle_uniform(cfg, n_traces):
     return bins, dt, outs
 
 
+def oracle_uniform_sample(cfg, x, pick, taps, max_bins=None):
+    """Time the oracle on traces `pick` of a uniform batch, optionally on an
+    evenly strided subset of each transform's bins: (bins, s, {kind: out},
+    {kind: bin indices})."""
+    from oracle import spec_oracle as O
+
+    def sub(total):
+        if max_bins is None or total <= max_bins:
+            return np.arange(total)
+        return np.unique(np.linspace(0, total - 1, max_bins).round().astype(np.int64))
+
+    xs = x[pick]
+    h = np.asarray(taps, dtype=np.float64)
+    kb = {"fft": sub(cfg.n_fft // 2 + 1), "czt": sub(cfg.czt_m), "zoom": sub(cfg.zoom_n_fft // cfg.zoom_d)}
+    t0 = time.perf_counter()
+    outs = {"fft": O.fft_padded_bins(xs, cfg.n_fft, kb["fft"]),
+            "czt": O.czt_bins(xs, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, kb["czt"]),
+            "zoom": O.zoom_bins(xs, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, h, cfg.zoom_n_fft, kb["zoom"])}
+    dt = time.perf_counter() - t0
+    return len(pick) * sum(len(v) for v in kb.values()), dt, outs, kb
+
+
 def oracle_ragged(items, traces, pick, max_bins=None):
     """Time the oracle on the picked ragged traces: (bins, s, {kind: {i: out}}).
     With ``max_bins`` each transform evaluates at most that many of its bins,
@@ -330,35 +397,54 @@ def run_reference(args):
 # --------------------------------------------------------------- workloads --
 
 class Uniform:
-    """Workload 1: 4096 traces x 2048 samples, one launch per transform."""
+    """Workloads 1, 3 and 4: a batch of equal traces, one launch sequence per
+    transform (1: 4096 x 2048 samples; 3: 65536 x 1024, chirp-z on the
+    tensor cores; 4: 256 x 262144, multi-pass FFT and chirp-z)."""
 
-    def __init__(self, spec, ctx, dev):
+    def __init__(self, spec, ctx, dev, workload=1):
         import torch
-        cfg = self.cfg = synth.UNIFORM[1]
+        self.workload = workload
+        cfg = self.cfg = synth.UNIFORM[workload]
         B = self.B = cfg.batch
         self.spec, self.ctx = spec, ctx
-        self.x = synth.batch_traces(1, range(B))
+        if workload == 3:
+            # 64 copies of 1024 distinct traces keep the host-side generation short
+            base = synth.batch_traces(3, range(1024))
+            self.x = np.ascontiguousarray(np.tile(base, (B // 1024, 1)))
+        else:
+            self.x = synth.batch_traces(workload, range(B))
         self.xd = torch.from_numpy(self.x).to(dev)
         self.taps_h = spec.spec_design_lowpass(cfg.zoom_taps, cfg.zoom_d)
         self.taps_d = torch.from_numpy(self.taps_h).to(dev)
+        self.czt_mode = spec.SPEC_CZT_GEMM_F16X3 if workload == 3 else spec.SPEC_CZT_AUTO
         c = {"fft": trace_cost("fft", cfg.n, cfg.n_fft),
-             "czt": trace_cost("czt", cfg.n, m=cfg.czt_m),
+             "czt": trace_cost("czt_gemm" if workload == 3 else "czt", cfg.n, m=cfg.czt_m),
              "zoom": trace_cost("zoom", cfg.n, cfg.zoom_n_fft, d=cfg.zoom_d, taps=cfg.zoom_taps)}
         self.bins = {k: B * v[0] for k, v in c.items()}
         self.bytes = {k: B * v[1] for k, v in c.items()}
         self.flops = {k: B * v[2] for k, v in c.items()}
+        self.bound = {"fft": "hbm", "czt": "tensor" if workload == 3 else "alu", "zoom": None}
         self.out = {k: torch.empty((B, c[k][0]), dtype=torch.complex64, device=dev) for k in c}
-        self.name = W1_NAME
+        self.name = {1: W1_NAME, 3: W3_NAME, 4: W4_NAME}[workload]
 
     def parts(self):
         s, ctx, cfg, o = self.spec, self.ctx, self.cfg, self.out
         return [("fft", lambda: s.spec_fft(ctx, self.xd, cfg.fs, cfg.n_fft, out=o["fft"])),
-                ("czt", lambda: s.spec_czt(ctx, self.xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, out=o["czt"])),
+                ("czt", lambda: s.spec_czt(ctx, self.xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m,
+                                           mode=self.czt_mode, out=o["czt"])),
                 ("zoom", lambda: s.spec_zoom(ctx, self.xd, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d,
                                              self.taps_d, cfg.zoom_n_fft, out=o["zoom"]))]
 
     def launches(self):
-        return 3
+        """Kernels of ours launched per step."""
+        if self.workload == 1:
+            return 3
+        if self.workload == 3:
+            return 4                 # FFT, split + product, Zoom
+        # long traces: FFT 2 per 128-trace chunk, chirp-z 3 per chunk, Zoom FIR + FFT
+        chunks_fft = -(-self.B // max(1, (1 << 30) // (8 * self.cfg.n_fft // 2)))
+        chunks_czt = -(-self.B // max(1, (1 << 30) // (8 * (1 << 19))))
+        return 2 * chunks_fft + 3 * chunks_czt + 2
 
     def e2e(self):
         """End-to-end step through the C-ABI with pinned host buffers."""
@@ -371,7 +457,7 @@ class Uniform:
 
         def step():
             s.spec_fft(ctx, xn, cfg.fs, cfg.n_fft, out=hn["fft"])
-            s.spec_czt(ctx, xn, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, out=hn["czt"])
+            s.spec_czt(ctx, xn, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, mode=self.czt_mode, out=hn["czt"])
             s.spec_zoom(ctx, xn, cfg.fs, cfg.zoom_f1, cfg.zoom_f2, cfg.zoom_d, self.taps_h, cfg.zoom_n_fft,
                         out=hn["zoom"])
 
@@ -382,15 +468,28 @@ class Uniform:
         return step, check, h2d, d2h
 
     def cpu_leg(self):
-        b, dt, ref = oracle_uniform(self.cfg, self.B)
+        if self.workload == 1:
+            b, dt, ref = oracle_uniform(self.cfg, self.B)
+            errs = {}
+            for k, got in self.out.items():
+                g = got.cpu().numpy().astype(np.complex128)
+                errs[k] = float((np.linalg.norm(g - ref[k], axis=1) / np.linalg.norm(ref[k], axis=1)).max())
+            cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
+                   "sample": f"the whole batch ({self.B} traces), all bins of FFT, CZT and Zoom FFT, FP64 numpy, "
+                             f"{dt:.1f} s"}
+            return cpu, errs, "max_rel_l2_all_traces"
+        # workloads 3 and 4: a bounded sample (traces; bins for the long traces)
+        pick = [0, 1, 2, 3] if self.workload == 4 else list(range(0, 1024, 16))
+        max_bins = 512 if self.workload == 4 else None
+        b, dt, ref, kb = oracle_uniform_sample(self.cfg, self.x, pick, self.taps_h, max_bins)
         errs = {}
         for k, got in self.out.items():
-            g = got.cpu().numpy().astype(np.complex128)
+            g = got[pick].cpu().numpy().astype(np.complex128)[:, kb[k]]
             errs[k] = float((np.linalg.norm(g - ref[k], axis=1) / np.linalg.norm(ref[k], axis=1)).max())
+        what = "all bins" if max_bins is None else f"at most {max_bins} evenly strided bins of each transform"
         cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"the whole batch ({self.B} traces), all bins of FFT, CZT and Zoom FFT, FP64 numpy, "
-                         f"{dt:.1f} s"}
-        return cpu, errs, "max_rel_l2_all_traces"
+               "sample": f"{len(pick)} of {self.B} traces, {what}, FP64 numpy, {dt:.1f} s"}
+        return cpu, errs, "max_rel_l2_sampled"
 
 
 class Ragged:
@@ -424,6 +523,7 @@ class Ragged:
             self.descs[name] = (kind, [spec.spec_desc(int(xo[i]), it.n, int(oo[i]), it.f1, it.f2, it.n_fft, it.m,
                                                       it.d, int(to[i]), it.n_taps) for i, it in enumerate(self.items)])
             self.out[name] = torch.empty(int(nb.sum()), dtype=torch.complex64, device=dev)
+        self.bound = {}
         self.name = W2_NAME
 
     def parts(self):
@@ -489,7 +589,14 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = spec.Context(local)
-    W = Ragged(spec, ctx, dev) if args.workload == 2 else Uniform(spec, ctx, dev)
+    W = Ragged(spec, ctx, dev) if args.workload == 2 else Uniform(spec, ctx, dev, args.workload)
+    fp32_peak, fp32_src = FP32_PEAK_TFLOPS, "nominal 152 SM x 128 lanes x 2 x 2.07 GHz"
+    try:
+        meas = spec.spec_measure_fp32_peak(ctx)
+        if meas > 0:
+            fp32_peak, fp32_src = meas, "measured (packed FP32 FMA microbenchmark, this run)"
+    except Exception:
+        pass
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     parts = W.parts()
@@ -547,28 +654,59 @@ def run_ours(args):
         return 0
 
     hbm, hbm_kind = measured_peaks()
+    tensor_peak, tensor_src = measured_tensor_peak()
     kern = {}
     for name, _ in parts:
         ms = statistics.median(per[name])
-        gbs = W.bytes[name] / (ms / 1e3) / 1e9
-        tfl = W.flops[name] / (ms / 1e3) / 1e12
-        kern[name] = {"ms": ms, "bins_per_s": W.bins[name] / (ms / 1e3), "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
-                      "fp32_tflops": tfl, "fp32_frac": tfl / FP32_PEAK_TFLOPS}
+        sec = ms / 1e3
+        gbs = W.bytes[name] / sec / 1e9
+        tfl = W.flops[name] / sec / 1e12
+        k = {"ms": ms, "bins_per_s": W.bins[name] / sec, "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
+        t_hbm = W.bytes[name] / (hbm * 1e9)
+        if W.bound.get(name) == "tensor":
+            k.update(tensor_tflops=tfl, tensor_frac=tfl / tensor_peak)
+            t_cmp, cmp_name = W.flops[name] / (tensor_peak * 1e12), "tensor"
+        else:
+            k.update(fp32_tflops=tfl, fp32_frac=tfl / fp32_peak)
+            t_cmp, cmp_name = W.flops[name] / (fp32_peak * 1e12), "alu"
+        # the binding roof is the one with the longer attainable time
+        k["bound"] = "hbm" if t_hbm >= t_cmp else cmp_name
+        k["frac"] = max(t_hbm, t_cmp) / sec
+        kern[name] = k
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    if kern[dom]["hbm_frac"] >= kern[dom]["fp32_frac"]:
-        roof = {"bound": "hbm", "achieved": kern[dom]["hbm_gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": kern[dom]["hbm_frac"], "traffic": None, "kernel": dom,
-                "peak_source": f"{hbm_kind} hbm_gbs"}
+    kd = kern[dom]
+    if kd["bound"] == "hbm":
+        roof = {"bound": "hbm", "achieved": kd["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": kd["hbm_frac"],
+                "peak_source": f"{hbm_kind} hbm_gbs (of {hbm_kind})"}
+    elif kd["bound"] == "tensor":
+        roof = {"bound": "tensor", "achieved": kd["tensor_tflops"], "peak": tensor_peak, "unit": "TFLOP/s",
+                "frac": kd["tensor_frac"], "peak_source": tensor_src}
     else:
-        roof = {"bound": "alu", "achieved": kern[dom]["fp32_tflops"], "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": kern[dom]["fp32_frac"], "traffic": None, "kernel": dom,
-                "peak_source": "FP32 FMA 152 SM x 128 x 2 x 2.07 GHz"}
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file) and args.workload == 1:
-        with open(traffic_file) as f:
-            tr = json.load(f).get(dom)
-        if tr and tr.get("per_launch_bytes"):
-            roof["traffic"] = tr["per_launch_bytes"]
+        roof = {"bound": "alu", "achieved": kd["fp32_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": kd["fp32_frac"], "peak_source": fp32_src}
+    roof["kernel"] = dom
+    roof["traffic"] = traffic_for(args.workload, dom)
+
+    # cuFFT beside our FFT (a reported comparison, not the target):
+    # torch.fft.rfft(x, n=N_FFT), which pads internally, same timing protocol
+    lib_cmp = None
+    if hasattr(W, "cfg") and world == 1:
+        try:
+            n_fft = W.cfg.n_fft
+            ts = []
+            for it in range(8):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                torch.fft.rfft(W.xd, n=n_fft)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= 3:
+                    ts.append(e0.elapsed_time(e1))
+            lib_cmp = {"cufft_rfft_ms": statistics.median(ts), "ours_fft_ms": kern["fft"]["ms"],
+                       "what": "torch.fft.rfft(x, n=N_FFT) on the same device batch (cuFFT; pads internally)"}
+        except Exception as ex:              # a comparison only; never fails the bench
+            lib_cmp = {"unavailable": str(ex)[:120]}
 
     # CPU-baseline leg (rank 0, N = 1 only): the FP64 oracle, timed; its
     # outputs also give the parity of the timed GPU outputs.
@@ -592,6 +730,7 @@ def run_ours(args):
                 "steps": e2e_steps, "max_abs_diff_vs_device_path": e2e_diff},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
+        "library_comparison": lib_cmp,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -605,7 +744,7 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2])
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

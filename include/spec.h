@@ -92,6 +92,12 @@ SPEC_API const char* spec_last_error(const spec_ctx* ctx);
  * clears it. */
 SPEC_API spec_status spec_ctx_check(spec_ctx* ctx, void* stream);
 
+/* Measure the device's FP32 FMA throughput (TFLOP/s) with a packed-FMA
+ * microbenchmark (a few ms; synchronises `stream`).  The denominator of the
+ * ALU roofline reported for the FP32 transforms.  No counterpart in the
+ * paper. */
+SPEC_API spec_status spec_measure_fp32_peak(spec_ctx* ctx, double* tflops, void* stream);
+
 /* Self-test of the bounded-wait machinery: launches one CTA that waits on
  * a barrier nothing will complete, with a limit of `timeout_us`
  * microseconds (1 .. 10^6).  The next spec_ctx_check on `stream` must then

@@ -37,10 +37,96 @@ struct FftArgs {
     float2* X;
     int64_t ld_X;
     const RaggedItem* items;   // ragged batch: per-trace x / X offsets and n (else null)
+    int paired;                // C > 1 without a cluster: each CTA owns residue pairs {r, R - r}
 };
 
+// Residue of local FFT rl in CTA `rank` of a trace.  Contiguous by default.
+// With `paired` (no cluster), CTA c owns a run of g = Rc/2 consecutive
+// residues c g .. c g + g - 1 (local 0 .. g-1) and their mirrors R - r
+// (local g .. 2g-1; CTA 0 holds 0 and R/2, both their own mirrors), so every
+// partner Z[H - k] of its Z[k] is local and its outputs form runs of g.
+__device__ __forceinline__ int residue_of(const FftArgs& a, int rank, int rl) {
+    if (!a.paired) return rank * a.Rc + rl;
+    if (a.Rc == 1) return rank;                                   // R = 2: both residues self-paired
+    const int R = 1 << a.logR;
+    const int g = a.Rc >> 1;
+    if (rl < g) return rank * g + rl;
+    const int j = rl - g;
+    return (rank == 0 && j == 0) ? R / 2 : R - (rank * g + j);
+}
+
+// Cluster staging for the unpack.  CTA c of a cluster of C unpacks the pairs
+// k in [c P, c P + P), P = H/(2C) (the last CTA also k = H/2), so it receives
+// exactly the values those pairs read: Z[k] at slot k - c P (0 .. P) and
+// Z[H - k] at slot P + 1 + (k - c P).  Every value crosses the cluster once,
+// as a remote store; the unpack then reads only its own shared memory.
+__device__ __forceinline__ int2 pair_home(int j, int H, int logP, int C) {
+    const int half = H >> 1;
+    if (j <= half) {
+        const int c = min(j >> logP, C - 1);
+        return make_int2(c, j - (c << logP));
+    }
+    const int kk = H - j;
+    const int c = kk >> logP;
+    return make_int2(c, (1 << logP) + 1 + kk - (c << logP));
+}
+
+// Store v at element `idx` of the same shared array in CTA `cta` of the
+// cluster (distributed shared memory through the shared-memory path).
+__device__ __forceinline__ void dsmem_store(float2* local_base, int idx, unsigned cta, float2 v) {
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(local_base + idx);
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(cta));
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// Cluster barrier whose arrival does not order this thread's memory accesses
+// (used where only the completion of already-consumed reads matters).
+__device__ __forceinline__ void cluster_arrive_relaxed_wait() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
+// X[k] and X[H - k] from A = Z[k], B = Z[H - k] (Section 2.1 real-input unpack)
+__device__ __forceinline__ void unpack_pair(float2* Xr, int k, int H, float2 A, float2 B, float2 w) {
+    const float2 sp = mul2(make_float2(A.x + B.x, A.y - B.y), make_float2(0.5f, 0.5f));
+    const float2 dm = mul2(make_float2(A.x - B.x, A.y + B.y), make_float2(0.5f, 0.5f));
+    const float2 wd = cmul(w, dm);
+    Xr[k] = make_float2(sp.x + wd.y, sp.y - wd.x);
+    if (H - k != k) Xr[H - k] = make_float2(sp.x - wd.y, -sp.y - wd.x);
+}
+
+// Packed input of one residue FFT, pre-twiddled: v[i] = z[m] w_H^{r m},
+// z[m] = x[2m] + j x[2m+1], m = t + T i, the twiddle w_H^{r t} w_H^{r T i}.
+template <int E, int T>
+__device__ __forceinline__ void load_pretwiddled(float2 (&v)[E], const float* xr, int n, bool live,
+                                                 const float2* wt_p, const float2* wi_p, int t) {
+    const float2 wt = __ldg(wt_p);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int m = t + T * i;
+        float re = 0.f, im = 0.f;
+        if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+        if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+        v[i] = cmul(make_float2(re, im), cmul(wt, __ldg(wi_p + i)));
+    }
+}
+
+__device__ __forceinline__ unsigned opaque_tid() {
+    unsigned v;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(v));
+    return v;
+}
+__device__ __forceinline__ unsigned opaque_ctaid() {
+    unsigned v;
+    asm volatile("mov.u32 %0, %%ctaid.x;" : "=r"(v));
+    return v;
+}
+
+template <int E, int T>
+__device__ __forceinline__ void epilogue(const FftArgs& a, float2 (&v)[E]);
+
 template <int LZ, int EMAX>
-__global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(FftArgs a) {
+__global__ void __launch_bounds__(EMAX == 32 ? 256 : 1024, EMAX == 32 ? 2 : 1) k_fft_real_padded(FftArgs a) {
     using FFT = BlockFFT<LZ, false, float2, EMAX>;
     constexpr int E = FFT::E;
     constexpr int T = FFT::T;
@@ -64,76 +150,133 @@ __global__ void __launch_bounds__(EMAX == 32 ? 256 : 512, 2) k_fft_real_padded(F
         n = it.n;
     }
     const int R = 1 << a.logR;
-    const int r = rank * a.Rc + rl;              // residue of this thread's FFT
-    const int H = a.H;
+    const int r = residue_of(a, rank, rl);       // residue of this thread's FFT
     float2* zs = smem + f * a.trace_smem;        // this trace's shared memory
     float2* s = zs + rl * padded_len(LZ);
 
     // 1-2. packed, pre-twiddled input: v[i] = z[m] w_H^{r m}, m = t + T i.
     float2 v[E];
-    {
-        const float2 wt = __ldg(a.tab + r * T + t);
-        const float2* wi = a.tab + R * T + r * E;
-        const float* xr = a.x + xo;
+    load_pretwiddled<E, T>(v, a.x + xo, n, live, a.tab + r * T + t, a.tab + R * T + r * E, t);
+    FFT::run(v, s, t, a.tw);
+    // From here on, the thread's placement is derived again from fresh reads
+    // of its indices (opaque to the compiler), so that only v[] is live
+    // across the FFT (register pressure at 64 registers).
+    epilogue<E, T>(a, v);
+}
+
+// Unpack of a CTA that owns residue pairs (no cluster): each residue's Z in
+// natural order in its own shared region, then every output pair (k, H - k)
+// with k in its residues from local values.  X is written at stride R.
+template <int E, int T>
+__device__ __forceinline__ void paired_unpack(const FftArgs& a, float2 (&v)[E], float2* zs, int rl, int t, int lt,
+                                              int per_trace, bool live, int64_t Xo) {
+    constexpr int LZ = E * T;
+    const int R = 1 << a.logR;
+    const int H = a.H;
+    __syncthreads();                                     // every FFT's exchanges are done
+    float2* s = zs + rl * padded_len(LZ);
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + T * i;
-            float re = 0.f, im = 0.f;
-            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
-            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
-            v[i] = cmul(make_float2(re, im), cmul(wt, __ldg(wi + i)));
+    for (int i = 0; i < E; ++i) s[pidx(t + T * i)] = v[i];
+    __syncthreads();
+    if (!live) return;
+    float2* Xr = a.X + Xo;
+    const float2* wp = a.tab + R * T + R * E;
+    const int rank = a.C > 1 ? (int)(opaque_ctaid() % a.C) : 0;
+    // (k, A = Z[k], B = Z[H - k]) -> X[k], X[H - k] with the twiddle of min(k, H - k)
+    auto emit = [&](int k, float2 A, float2 B) {
+        if (2 * k <= H) unpack_pair(Xr, k, H, A, B, __ldg(wp + k));
+        else unpack_pair(Xr, H - k, H, B, A, __ldg(wp + (H - k)));
+    };
+    if (a.Rc == 1) {
+        // R = 2: residue 0 (CTA 0) and residue 1 = R/2 (CTA 1), each its own mirror
+        for (int q = lt; q <= LZ / 2; q += per_trace) {
+            if (rank == 0) emit(R * q, zs[pidx(q)], zs[pidx((LZ - q) & (LZ - 1))]);
+            else if (q < LZ / 2) emit(R * q + 1, zs[pidx(q)], zs[pidx(LZ - 1 - q)]);
+        }
+        return;
+    }
+    const int g = a.Rc >> 1;
+    const int lg = __ffs(g) - 1;
+    // the run: residue r = rank g + j (slot j) with mirror R - r (slot g + j);
+    // consecutive threads take consecutive j, so X is written in runs of g
+    for (int idx = lt; idx < g * LZ; idx += per_trace) {
+        const int j = idx & (g - 1);
+        const int q = idx >> lg;
+        if (rank == 0 && j == 0) continue;                       // residue 0: below
+        emit(R * q + rank * g + j, zs[j * padded_len(LZ) + pidx(q)], zs[(g + j) * padded_len(LZ) + pidx(LZ - 1 - q)]);
+    }
+    if (rank == 0) {
+        // residue 0 (slot 0): Z[Rq] with Z[R(LZ - q)]; residue R/2 (slot g): position q with LZ-1-q
+        const float2* s0 = zs;
+        const float2* sh = zs + g * padded_len(LZ);
+        for (int q = lt; q <= LZ / 2; q += per_trace) {
+            emit(R * q, s0[pidx(q)], s0[pidx((LZ - q) & (LZ - 1))]);
+            if (q < LZ / 2) emit(R * q + R / 2, sh[pidx(q)], sh[pidx(LZ - 1 - q)]);
         }
     }
-    FFT::run(v, s, t, a.tw);
+}
 
-    // v[i] = Z[R q + r], q = t + T i.  Stage Z in natural order; CTA c of a
-    // cluster owns Z[c chunk .. (c+1) chunk).
-    const int chunk_mask = (1 << a.logChunk) - 1;
-    // Every CTA of a cluster must have finished its FFT (whose exchanges use
-    // this shared memory) before any of them writes Z into its peers.
-    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
+template <int E, int T>
+__device__ __forceinline__ void epilogue(const FftArgs& a, float2 (&v)[E]) {
+    extern __shared__ float2 smem[];
+    const int per_trace = a.Rc * T;
+    const int tid = (int)opaque_tid();
+    const int f = tid / per_trace;
+    const int lt = tid - f * per_trace;
+    const int rl = lt / T;
+    const int t = lt - rl * T;
+    const unsigned cta = opaque_ctaid();
+    const int rank = a.C > 1 ? (int)(cta % a.C) : 0;
+    const int64_t b = (int64_t)(cta / a.C) * a.F + f;
+    const bool live = b < a.batch;
+    const int64_t Xo = !live ? 0 : a.items ? a.items[b].out_off : b * a.ld_X;
+    const int R = 1 << a.logR;
+    const int r = residue_of(a, rank, rl);
+    const int H = a.H;
+    float2* zs = smem + f * a.trace_smem;
+    if (a.paired) {
+        paired_unpack<E, T>(a, v, zs, rl, t, lt, per_trace, live, Xo);
+        return;
+    }
+
+    // v[i] = Z[R q + r], q = t + T i.  Every CTA of a cluster must have
+    // finished its FFT (whose exchanges use this shared memory) before any of
+    // them writes Z into its peers: their last exchange reads have been
+    // consumed by the arithmetic before their arrival, so a relaxed arrive
+    // suffices for that ordering.
+    if (a.C > 1) cluster_arrive_relaxed_wait(); else __syncthreads();
     if (a.C == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
         __syncthreads();
     } else {
         cg::cluster_group cl = cg::this_cluster();
+        const int logP = a.logChunk - 1;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            const int k = ((t + T * i) << a.logR) + r;
-            float2* dst = cl.map_shared_rank(zs, k >> a.logChunk);
-            dst[pidx(k & chunk_mask)] = v[i];
+            const int2 h = pair_home(((t + T * i) << a.logR) + r, H, logP, a.C);
+            dsmem_store(zs, pidx(h.y), (unsigned)h.x, v[i]);
         }
         cl.sync();
     }
 
-    // 3. unpack pairs (k, H - k), k = 0 .. H/2, split over the cluster.
-    const int pairs = H / 2 + 1;
-    const int per_cta = (pairs + a.C - 1) / a.C;
-    const int k0 = rank * per_cta;
-    const int k1 = min(pairs, k0 + per_cta);
+    // 3. unpack pairs (k, H - k): X[k] = (A + conj B)/2 - j/2 w (A - conj B),
+    //    w = e^{-j 2 pi k/N_FFT}; X[H-k] mirrors it.
     float2* Xr = a.X + Xo;
     const float2* wp = a.tab + R * T + R * E;
-    for (int k = k0 + lt; k < k1 && live; k += per_trace) {
-        const int kb = (H - k) & (H - 1);
-        float2 A, B;
-        if (a.C == 1) {
-            A = zs[pidx(k)];
-            B = zs[pidx(kb)];
-        } else {
-            cg::cluster_group cl = cg::this_cluster();
-            A = cl.map_shared_rank(zs, k >> a.logChunk)[pidx(k & chunk_mask)];
-            B = cl.map_shared_rank(zs, kb >> a.logChunk)[pidx(kb & chunk_mask)];
+    if (a.C == 1) {
+        for (int k = lt; k <= H / 2 && live; k += per_trace)
+            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], __ldg(wp + k));
+    } else {
+        const int P = (H >> 1) / a.C;
+        const int k0 = rank * P;
+        const int k1 = k0 + P + (rank == a.C - 1 ? 1 : 0);
+        for (int k = k0 + lt; k < k1 && live; k += per_trace) {
+            const float2 A = zs[pidx(k - k0)];
+            const float2 B = (k == 0 || 2 * k == H) ? A : zs[pidx(P + 1 + (k - k0))];
+            unpack_pair(Xr, k, H, A, B, __ldg(wp + k));
         }
-        const float2 w = __ldg(wp + k);                     // e^{-j 2 pi k/N_FFT}
-        // X[k] = (A + conj B)/2 - j/2 w (A - conj B); X[H-k] mirrors it
-        const float2 sp = mul2(make_float2(A.x + B.x, A.y - B.y), make_float2(0.5f, 0.5f));
-        const float2 dm = mul2(make_float2(A.x - B.x, A.y + B.y), make_float2(0.5f, 0.5f));
-        const float2 wd = cmul(w, dm);
-        Xr[k] = make_float2(sp.x + wd.y, sp.y - wd.x);
-        if (H - k != k) Xr[H - k] = make_float2(sp.x - wd.y, -sp.y - wd.x);
     }
-    if (a.C > 1) cg::this_cluster().sync();   // keep shared memory alive for readers
 }
 
 // Two-lane variant: each thread carries residues ra and ra + Rc/2 of one
@@ -190,10 +333,9 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     }
     FFT::run(v, s, t, a.tw);
 
-    const int chunk_mask = (1 << a.logChunk) - 1;
     // Every CTA of a cluster must have finished its FFT (whose exchanges use
     // this shared memory) before any of them writes Z into its peers.
-    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
+    if (a.C > 1) cluster_arrive_relaxed_wait(); else __syncthreads();
     if (a.C == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -204,41 +346,33 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
         __syncthreads();
     } else {
         cg::cluster_group cl = cg::this_cluster();
+        const int logP = a.logChunk - 1;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int q = (t + T * i) << a.logR;
-            const int ka = q + ra, kb = q + rb;
-            cl.map_shared_rank(zs, ka >> a.logChunk)[pidx(ka & chunk_mask)] = lane_a(v[i]);
-            cl.map_shared_rank(zs, kb >> a.logChunk)[pidx(kb & chunk_mask)] = lane_b(v[i]);
+            const int2 ha = pair_home(q + ra, H, logP, a.C);
+            const int2 hb = pair_home(q + rb, H, logP, a.C);
+            dsmem_store(zs, pidx(ha.y), (unsigned)ha.x, lane_a(v[i]));
+            dsmem_store(zs, pidx(hb.y), (unsigned)hb.x, lane_b(v[i]));
         }
         cl.sync();
     }
 
-    const int pairs = H / 2 + 1;
-    const int per_cta = (pairs + a.C - 1) / a.C;
-    const int k0 = rank * per_cta;
-    const int k1 = min(pairs, k0 + per_cta);
     float2* Xr = a.X + Xo;
     const float2* wp = a.tab + R * T + R * E;
-    for (int k = k0 + lt; k < k1 && live; k += per_trace) {
-        const int kb = (H - k) & (H - 1);
-        float2 A, B;
-        if (a.C == 1) {
-            A = zs[pidx(k)];
-            B = zs[pidx(kb)];
-        } else {
-            cg::cluster_group cl = cg::this_cluster();
-            A = cl.map_shared_rank(zs, k >> a.logChunk)[pidx(k & chunk_mask)];
-            B = cl.map_shared_rank(zs, kb >> a.logChunk)[pidx(kb & chunk_mask)];
+    if (a.C == 1) {
+        for (int k = lt; k <= H / 2 && live; k += per_trace)
+            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], __ldg(wp + k));
+    } else {
+        const int P = (H >> 1) / a.C;
+        const int k0 = rank * P;
+        const int k1 = k0 + P + (rank == a.C - 1 ? 1 : 0);
+        for (int k = k0 + lt; k < k1 && live; k += per_trace) {
+            const float2 A = zs[pidx(k - k0)];
+            const float2 B = (k == 0 || 2 * k == H) ? A : zs[pidx(P + 1 + (k - k0))];
+            unpack_pair(Xr, k, H, A, B, __ldg(wp + k));
         }
-        const float2 w = __ldg(wp + k);
-        const float2 sp = mul2(make_float2(A.x + B.x, A.y - B.y), make_float2(0.5f, 0.5f));
-        const float2 dm = mul2(make_float2(A.x - B.x, A.y + B.y), make_float2(0.5f, 0.5f));
-        const float2 wd = cmul(w, dm);
-        Xr[k] = make_float2(sp.x + wd.y, sp.y - wd.x);
-        if (H - k != k) Xr[H - k] = make_float2(sp.x - wd.y, -sp.y - wd.x);
     }
-    if (a.C > 1) cg::this_cluster().sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -261,6 +395,9 @@ struct C2cArgs {
     int64_t ld_X;
     const RaggedItem* items;   // ragged batch: nin = lout, u / X offsets (else null)
 };
+
+template <int E, int T>
+__device__ __forceinline__ void c2c_epilogue(const C2cArgs& a, float2 (&v)[E]);
 
 template <int LZ>
 __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
@@ -304,11 +441,29 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
         }
     }
     FFT::run(v, s, t, a.tw);
+    c2c_epilogue<E, T>(a, v);     // placement re-derived: only v[] is live across the FFT
+}
 
+template <int E, int T>
+__device__ __forceinline__ void c2c_epilogue(const C2cArgs& a, float2 (&v)[E]) {
+    extern __shared__ float2 smem[];
+    const int per_trace = a.Rc * T;
+    const int tid = (int)opaque_tid();
+    const int f = tid / per_trace;
+    const int lt = tid - f * per_trace;
+    const int rl = lt / T;
+    const int t = lt - rl * T;
+    const unsigned cta = opaque_ctaid();
+    const int rank = a.C > 1 ? (int)(cta % a.C) : 0;
+    const int64_t b = (int64_t)(cta / a.C) * a.F + f;
+    const bool live = b < a.batch;
+    const int64_t Xo = !live ? 0 : a.items ? a.items[b].out_off : b * a.ld_X;
+    const int r = rank * a.Rc + rl;
+    float2* zs = smem + f * a.trace_smem;
     const int chunk = 1 << a.logChunk;
     // Every CTA of a cluster must have finished its FFT (whose exchanges use
     // this shared memory) before any of them writes Z into its peers.
-    if (a.C > 1) cg::this_cluster().sync(); else __syncthreads();
+    if (a.C > 1) cluster_arrive_relaxed_wait(); else __syncthreads();
     if (a.C == 1) {
 #pragma unroll
         for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
@@ -318,7 +473,7 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int k = ((t + T * i) << a.logR) + r;
-            cl.map_shared_rank(zs, k >> a.logChunk)[pidx(k & (chunk - 1))] = v[i];
+            dsmem_store(zs, pidx(k & (chunk - 1)), (unsigned)(k >> a.logChunk), v[i]);
         }
         cl.sync();
     }
@@ -501,7 +656,13 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
         return false;
     }
     const int64_t R = H / LZ;
-    const int64_t C = std::max<int64_t>(1, H / kTile);
+    // Points per CTA: 16384 (1024 threads, one CTA per SM) when the residue
+    // FFTs are long, which keeps 32768-point transforms in one CTA and halves
+    // the CTAs of 65536-point ones; 8192 otherwise (measured on GB300: 79 vs
+    // 101 ns per 4096-sample trace to 32768 points, 213 vs 191 ns per
+    // 2048-sample trace to 65536 points).
+    const int64_t tile = LZ >= 2048 ? 2 * kTile : kTile;
+    const int64_t C = std::max<int64_t>(1, H / tile);
     if (C > 8) {
         *why = "padded FFT: n_fft above 131072 needs the multi-pass path";
         return false;
@@ -516,7 +677,11 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     p->Rc = (int)(R / C);
     p->E = E;
     p->T = T;
-    p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096 && p->emax == 16;
+    // C > 1: CTAs own residue pairs and unpack alone (no cluster) when every
+    // CTA can hold whole pairs; otherwise a cluster exchanges Z through
+    // distributed shared memory
+    p->paired = C > 1 && (p->Rc % 2 == 0 || (p->Rc == 1 && R == 2));
+    p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096 && p->emax == 16 && !p->paired && (p->Rc / 2) * T <= 256;
     const int per_trace = p->dual ? (p->Rc / 2) * T : p->Rc * T;
     p->F = 1;
     if (C == 1) {
@@ -525,7 +690,8 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
         p->F = (int)F;
     }
     const int chunk = (int)(H / C);
-    p->trace_smem = std::max(p->Rc * padded_len((int)LZ), padded_len(chunk));
+    // the cluster staging uses padded slots 0 .. chunk (pidx(chunk) = padded_len(chunk))
+    p->trace_smem = std::max(p->Rc * padded_len((int)LZ), padded_len(chunk) + 1);
     p->trace_smem += p->trace_smem & 1;       // keep float4 views 16-byte aligned
     p->threads = p->F * per_trace;
     p->smem = (size_t)p->F * p->trace_smem * sizeof(float2);
@@ -566,6 +732,7 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
     a.logChunk = ilog2(p.H / p.C); a.trace_smem = p.trace_smem;
     a.tw = tw; a.tab = tab;
     a.X = X; a.ld_X = ld_X; a.items = items;
+    a.paired = p.paired ? 1 : 0;
     const int per_trace = dual ? (p.Rc / 2) * p.T : p.Rc * p.T;
     int F = 1;
     if (p.C == 1) F = (int)std::min<int64_t>(std::max(1, 256 / per_trace), std::max<int64_t>(1, batch));
@@ -582,7 +749,7 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
     cudaLaunchAttribute attr[1];
     cfg.attrs = attr;
     cfg.numAttrs = 0;
-    if (p.C > 1) {
+    if (p.C > 1 && !p.paired) {
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = p.C;
         attr[0].val.clusterDim.y = 1;

@@ -53,6 +53,7 @@ struct FftPlan {
     int E = 0, T = 0;   // elements per thread, threads per residue FFT
     int F = 0;      // traces per CTA (C == 1 only)
     bool dual = false;  // two residues per thread (packed lanes)
+    bool paired = false;  // C > 1 CTAs own residue pairs {r, R - r}: no cluster, local unpack
     int emax = 16;      // elements per thread (16 or 32: radix of the passes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;

@@ -26,7 +26,7 @@ _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "
            SPEC_EUNSUPPORTED: "SPEC_EUNSUPPORTED", SPEC_ETIMEOUT: "SPEC_ETIMEOUT"}
 
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
-           "spec_selftest_wait_timeout",
+           "spec_selftest_wait_timeout", "spec_measure_fp32_peak",
            "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static", "spec_ragged", "spec_ragged_launches",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
 
@@ -66,6 +66,8 @@ def lib():
     L.spec_last_error.restype = C.c_char_p
     L.spec_ctx_check.argtypes = [vp, vp]
     L.spec_ctx_check.restype = C.c_int
+    L.spec_measure_fp32_peak.argtypes = [vp, C.POINTER(dbl), vp]
+    L.spec_measure_fp32_peak.restype = C.c_int
     L.spec_selftest_wait_timeout.argtypes = [vp, i64, vp]
     L.spec_selftest_wait_timeout.restype = C.c_int
     L.spec_fft.argtypes = [vp, fp, i64, i64, i64, dbl, i64, fp, i64, vp]
@@ -283,3 +285,10 @@ def ctx_status(ctx: Context, stream=None) -> int:
 def spec_selftest_wait_timeout(ctx: Context, timeout_us: int, stream=None):
     """Launch the bounded-wait self-test; the next ctx_status is SPEC_ETIMEOUT."""
     ctx.check(lib().spec_selftest_wait_timeout(ctx.handle, int(timeout_us), _stream_handle(stream)))
+
+
+def spec_measure_fp32_peak(ctx: Context, stream=None) -> float:
+    """Measured FP32 FMA throughput of the context's device, TFLOP/s."""
+    out = C.c_double(0.0)
+    ctx.check(lib().spec_measure_fp32_peak(ctx.handle, C.byref(out), _stream_handle(stream)))
+    return out.value
