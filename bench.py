@@ -401,16 +401,16 @@ class Uniform:
     transform (1: 4096 x 2048 samples; 3: 65536 x 1024, chirp-z on the
     tensor cores; 4: 256 x 262144, multi-pass FFT and chirp-z)."""
 
-    def __init__(self, spec, ctx, dev, workload=1):
+    def __init__(self, spec, ctx, dev, workload=1, batch=None):
         import torch
         self.workload = workload
         cfg = self.cfg = synth.UNIFORM[workload]
-        B = self.B = cfg.batch
+        B = self.B = cfg.batch if batch is None else int(batch)
         self.spec, self.ctx = spec, ctx
         if workload == 3:
-            # 64 copies of 1024 distinct traces keep the host-side generation short
-            base = synth.batch_traces(3, range(1024))
-            self.x = np.ascontiguousarray(np.tile(base, (B // 1024, 1)))
+            # copies of 1024 distinct traces keep the host-side generation short
+            base = synth.batch_traces(3, range(min(B, 1024)))
+            self.x = np.ascontiguousarray(np.resize(base, (B, cfg.n)))
         else:
             self.x = synth.batch_traces(workload, range(B))
         self.xd = torch.from_numpy(self.x).to(dev)
@@ -426,6 +426,8 @@ class Uniform:
         self.bound = {"fft": "hbm", "czt": "tensor" if workload == 3 else "alu", "zoom": None}
         self.out = {k: torch.empty((B, c[k][0]), dtype=torch.complex64, device=dev) for k in c}
         self.name = {1: W1_NAME, 3: W3_NAME, 4: W4_NAME}[workload]
+        if B != cfg.batch:
+            self.name = f"{B} of the traces of: " + self.name
 
     def parts(self):
         s, ctx, cfg, o = self.spec, self.ctx, self.cfg, self.out
@@ -479,7 +481,7 @@ class Uniform:
                              f"{dt:.1f} s"}
             return cpu, errs, "max_rel_l2_all_traces"
         # workloads 3 and 4: a bounded sample (traces; bins for the long traces)
-        pick = [0, 1, 2, 3] if self.workload == 4 else list(range(0, 1024, 16))
+        pick = list(range(min(4, self.B))) if self.workload == 4 else list(range(0, min(self.B, 1024), 16))
         max_bins = 512 if self.workload == 4 else None
         b, dt, ref, kb = oracle_uniform_sample(self.cfg, self.x, pick, self.taps_h, max_bins)
         errs = {}
@@ -589,7 +591,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = spec.Context(local)
-    W = Ragged(spec, ctx, dev) if args.workload == 2 else Uniform(spec, ctx, dev, args.workload)
+    W = Ragged(spec, ctx, dev) if args.workload == 2 else Uniform(spec, ctx, dev, args.workload, args.batch)
     fp32_peak, fp32_src = FP32_PEAK_TFLOPS, "nominal 152 SM x 128 lanes x 2 x 2.07 GHz"
     try:
         meas = spec.spec_measure_fp32_peak(ctx)
@@ -747,6 +749,9 @@ def main(argv=None):
     ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="traces per step for workloads 1, 3 and 4 (a smaller case for profiling; "
+                         "the default is the workload's batch)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
