@@ -42,7 +42,8 @@ struct spec_ctx {
     int device = 0;
     std::string err;
     float2* block_tw = nullptr;          // BlockFFT twiddles of every size
-    int lanes = 1;                       // 1: one FFT per thread group; 2: two packed lanes where possible
+    int lanes = 0;                       // 0: per transform (two packed lanes for the padded FFT, one for the
+                                         // chirp-z and Zoom: measured fastest); 1 or 2: forced everywhere
     std::vector<FftEntry> fft;
     std::vector<CztEntry> czt;
     std::vector<GemmZEntry> gemm_z;

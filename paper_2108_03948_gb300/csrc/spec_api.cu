@@ -589,7 +589,7 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt multi-pass launch");
         return stage_out_finish(c, X, batch, m, ld_X, st, io);
     }
-    cudaError_t e = (czt_dual_ok(L) && c->lanes != 1)
+    cudaError_t e = (czt_dual_ok(L) && c->lanes == 2)
         ? czt_launch2(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st)
         : czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
@@ -640,7 +640,7 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
                             c->block_tw + block_twiddle_offset(p.fft.LZ), tab, io.X, ld_X, st);
     } else {
         e = zoom_launch(p, io.x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), io.X, ld_X, st,
-                        c->lanes);
+                        c->lanes == 2 ? 2 : 1);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
     return stage_out_finish(c, X, batch, K, ld_X, st, io);
