@@ -142,11 +142,10 @@ __global__ void __launch_bounds__(EMAX == 32 ? 256 : 1024, EMAX == 32 ? 2 : 1) k
     const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
     const bool live = b < a.batch;
     int n = a.n;
-    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    int64_t xo = (live ? b : 0) * a.ld_x;
     if (a.items && live) {
         const RaggedItem& it = a.items[b];
         xo = it.x_off;
-        Xo = it.out_off;
         n = it.n;
     }
     const int R = 1 << a.logR;
@@ -416,11 +415,10 @@ __global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
     const int64_t b = (int64_t)(blockIdx.x / a.C) * a.F + f;
     const bool live = b < a.batch;
     int nin = a.nin;
-    int64_t uo = (live ? b : 0) * a.ld_u, Xo = (live ? b : 0) * a.ld_X;
+    int64_t uo = (live ? b : 0) * a.ld_u;
     if (a.items && live) {
         const RaggedItem& it = a.items[b];
         uo = it.u_off;
-        Xo = it.out_off;
         nin = it.lout;
     }
     const int R = 1 << a.logR;
