@@ -399,7 +399,7 @@ template <int E, int T>
 __device__ __forceinline__ void c2c_epilogue(const C2cArgs& a, float2 (&v)[E]);
 
 template <int LZ>
-__global__ void __launch_bounds__(512, 2) k_fft_c2c_pruned(C2cArgs a) {
+__global__ void __launch_bounds__(1024, 1) k_fft_c2c_pruned(C2cArgs a) {
     using FFT = BlockFFT<LZ, false>;
     constexpr int E = FFT::E;
     constexpr int T = FFT::T;
@@ -459,26 +459,25 @@ __device__ __forceinline__ void c2c_epilogue(const C2cArgs& a, float2 (&v)[E]) {
     const int r = rank * a.Rc + rl;
     float2* zs = smem + f * a.trace_smem;
     const int chunk = 1 << a.logChunk;
-    // Every CTA of a cluster must have finished its FFT (whose exchanges use
-    // this shared memory) before any of them writes Z into its peers.
-    if (a.C > 1) cluster_arrive_relaxed_wait(); else __syncthreads();
-    if (a.C == 1) {
+    if (a.C > 1) {
+        // several CTAs per transform: each writes its own residues' outputs
+        // Y[(R q + r + shift) mod K] directly -- runs of Rc consecutive
+        // outputs at stride R, no exchange between the CTAs
+        if (live) {
+            float2* Xr = a.X + Xo;
 #pragma unroll
-        for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
-        __syncthreads();
-    } else {
-        cg::cluster_group cl = cg::this_cluster();
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int k = ((t + T * i) << a.logR) + r;
-            dsmem_store(zs, pidx(k & (chunk - 1)), (unsigned)(k >> a.logChunk), v[i]);
+            for (int i = 0; i < E; ++i) Xr[((((t + T * i) << a.logR) + r) + a.shift) & (a.K - 1)] = v[i];
         }
-        cl.sync();
+        return;
     }
+    // one CTA: stage U in natural order, then contiguous rotated stores
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E; ++i) zs[pidx(((t + T * i) << a.logR) + r)] = v[i];
+    __syncthreads();
     if (live) {
         float2* Xr = a.X + Xo;
-        const int j0 = rank * chunk;
-        for (int j = lt; j < chunk; j += per_trace) Xr[(j0 + j + a.shift) & (a.K - 1)] = zs[pidx(j)];
+        for (int j = lt; j < chunk; j += per_trace) Xr[(j + a.shift) & (a.K - 1)] = zs[pidx(j)];
     }
 }
 
@@ -509,7 +508,10 @@ bool c2c_plan(int64_t batch, int64_t nin, int64_t K, FftPlan* p, std::string* wh
         return false;
     }
     const int64_t R = K / LZ;
-    const int64_t C = std::max<int64_t>(1, K / kTile);
+    // up to 16384 points per CTA (1024 threads) for long residue FFTs; a
+    // larger K spreads the residues over C CTAs that store independently
+    const int64_t tile = LZ >= 2048 ? 2 * kTile : kTile;
+    const int64_t C = std::max<int64_t>(1, K / tile);
     if (C > 8) {
         *why = "pruned FFT: K above 65536 needs the multi-pass path";
         return false;
@@ -524,7 +526,7 @@ bool c2c_plan(int64_t batch, int64_t nin, int64_t K, FftPlan* p, std::string* wh
     const int per_trace = p->Rc * p->T;
     p->F = 1;
     if (C == 1) p->F = (int)std::min<int64_t>(std::max(1, 256 / per_trace), std::max<int64_t>(1, batch));
-    p->trace_smem = std::max(p->Rc * padded_len((int)LZ), padded_len((int)(K / C)));
+    p->trace_smem = C > 1 ? p->Rc * padded_len((int)LZ) : std::max(p->Rc * padded_len((int)LZ), padded_len((int)K));
     p->threads = p->F * per_trace;
     p->smem = (size_t)p->F * p->trace_smem * sizeof(float2);
     return true;
@@ -565,16 +567,8 @@ cudaError_t c2c_launch(const FftPlan& p, const float2* u, int64_t ld_u, int nin,
     cfg.blockDim = dim3(p.threads);
     cfg.dynamicSmemBytes = p.smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    cfg.attrs = attr;
-    cfg.numAttrs = 0;
-    if (p.C > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = p.C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.numAttrs = 1;
-    }
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;            // the CTAs of one transform never communicate
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
