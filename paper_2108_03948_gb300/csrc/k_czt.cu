@@ -67,6 +67,9 @@ struct BluesteinArgs {
     const float2* tw;
     const RaggedItem* items;   // ragged batch: per-trace placement, n, m, tables (else null)
     const float2* tables;      // ragged batch: per-trace tables pre | V | post at items[b].tab_off
+    int segs;                  // segmented: > 1 segments per trace (batch counts segments)
+    int seg_len;               // segmented: samples per segment P
+    int64_t n_total;           // segmented: samples per trace N
 };
 
 template <int L>
@@ -95,6 +98,15 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, F
         pre = a.tables + it.tab_off;
         V = pre + n;
         post = V + L;
+    }
+    if (a.segs > 1) {
+        // segment sg of trace tr: samples sg P .. sg P + P - 1 (the last may be
+        // shorter); its M-point spectrum goes to row b of the workspace
+        const int64_t bb = live ? b : 0;
+        const int64_t tr = bb / a.segs;
+        const int sg = (int)(bb - tr * a.segs);
+        xo = tr * a.ld_x + (int64_t)sg * a.seg_len;
+        n = (int)min((int64_t)a.seg_len, a.n_total - (int64_t)sg * a.seg_len);
     }
     const float* xr = a.x + xo;
 
@@ -238,6 +250,58 @@ cudaError_t czt_launch(const CztTables& t, const float* x, int64_t batch, int64_
     a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = X; a.ld_X = ld_X; a.F = F; a.tw = tw;
     const int64_t grid = (batch + F - 1) / F;
     bk<<<(unsigned)grid, F * T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Segmented chirp-z for N >> M: the trace is cut into S segments of P samples
+// and X[k] = sum_s z_k^{-s P} X_s[k] (Eq. 11 split over n = s P + n'), where
+// X_s is the chirp-z of segment s by the Bluestein kernel above (tables for
+// N = P, shared by every segment).  W holds X_s for every (trace, segment).
+cudaError_t czt_seg_launch(const CztTables& t, const float* x, int64_t batch, int64_t n_total, int64_t ld_x,
+                           int seg_len, int segs, const float2* tw, float2* W, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    BsKernel bk;
+    VKernel vk;
+    if (!kernels_for(t.L, &bk, &vk)) return cudaErrorInvalidValue;
+    const int T = t.L / 16;
+    const int64_t virt = batch * segs;
+    int F = std::max(1, 256 / T);
+    F = (int)std::min<int64_t>(F, virt);
+    const size_t smem = (size_t)F * padded_len(t.L) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    BluesteinArgs a = {};
+    a.x = x; a.batch = virt; a.n = t.n; a.ld_x = ld_x; a.m = t.m;
+    a.pre = t.pre; a.V = t.V; a.post = t.post; a.X = W; a.ld_X = t.m; a.F = F; a.tw = tw;
+    a.segs = segs; a.seg_len = seg_len; a.n_total = n_total;
+    bk<<<(unsigned)((virt + F - 1) / F), F * T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// X[b][k] = sum_s W[b s][k] e^{-j 2 pi (a + b_step k) s P}: the phase in
+// cycles is A s P + B k s P modulo one, exact in 64-bit fixed point
+// (A = frac(f1/fs), B = frac(step/fs)).
+__global__ void k_czt_combine(const float2* __restrict__ W, int segs, int m, int64_t batch, uint64_t A, uint64_t B,
+                              int64_t seg_len, float2* X, int64_t ld_X) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= batch * m) return;
+    const int64_t b = idx / m;
+    const int k = (int)(idx - b * m);
+    const float2* w = W + b * segs * (int64_t)m + k;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int sg = 0; sg < segs; ++sg) {
+        const uint64_t sp = (uint64_t)sg * (uint64_t)seg_len;
+        const float2 rot = unit_fixed(A * sp + B * ((uint64_t)k * sp), true);
+        acc = cadd(acc, cmul(__ldg(w + (int64_t)sg * m), rot));
+    }
+    X[b * ld_X + k] = acc;
+}
+
+cudaError_t czt_combine_launch(const float2* W, int segs, int m, int64_t batch, uint64_t A, uint64_t B,
+                               int64_t seg_len, float2* X, int64_t ld_X, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    const int64_t total = batch * m;
+    k_czt_combine<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(W, segs, m, batch, A, B, seg_len, X, ld_X);
     return cudaGetLastError();
 }
 

@@ -519,19 +519,30 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     std::string why, why_long;
     LongPlan lp;
     const bool one_pass = czt_supported(n, m, &why);
-    if (!one_pass && !long_czt_plan(n, m, &lp, &why_long)) return fail(c, SPEC_EUNSUPPORTED, why + "; " + why_long);
+    // N + M - 1 beyond one CTA: with M <= 8192 the trace is cut into segments
+    // of P = L' - M + 1 samples that each fit a one-CTA Bluestein of length L'
+    // (Section 2.3's sum split over n); otherwise the multi-pass Bluestein.
+    const bool segmented = !one_pass && m <= 8192;
+    const int seg_L = m <= 2048 ? 8192 : 16384;
+    const int64_t seg_P = seg_L - m + 1;
+    const int segs = segmented ? (int)((n + seg_P - 1) / seg_P) : 1;
+    if (!one_pass && !segmented && !long_czt_plan(n, m, &lp, &why_long))
+        return fail(c, SPEC_EUNSUPPORTED, why + "; " + why_long);
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
 
-    // Bluestein tables for (N, M, f1/fs, step/fs), cached
+    // Bluestein tables for (N, M, f1/fs, step/fs), cached (for a segmented
+    // transform: the tables of one segment, N = P)
     const double step = m > 1 ? (f2 - f1) / (double)(m - 1) : 0.0;
     const uint64_t A = cycles_to_fixed(f1 / fs);
     const uint64_t Bh = cycles_to_fixed(0.5 * (step / fs));
-    const int L = one_pass ? czt_length(n, m) : (1 << lp.logP);
+    const int64_t n_tab = segmented ? seg_P : n;
+    const bool tab_one_pass = one_pass || segmented;
+    const int L = one_pass ? czt_length(n, m) : segmented ? seg_L : (1 << lp.logP);
     CztEntry* en = nullptr;
     for (auto& it : c->czt)
-        if (it.t.n == n && it.t.m == m && it.t.L == L && it.t.A == A && it.t.Bh == Bh) en = &it;
+        if (it.t.n == n_tab && it.t.m == m && it.t.L == L && it.t.A == A && it.t.Bh == Bh) en = &it;
     if (!en) {
         if (c->czt.size() >= kCztCacheMax) {
             auto lru = std::min_element(c->czt.begin(), c->czt.end(),
@@ -542,17 +553,17 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
             c->czt.erase(lru);
         }
         CztEntry ne;
-        ne.t.n = (int)n; ne.t.m = (int)m; ne.t.L = L; ne.t.A = A; ne.t.Bh = Bh;
-        ne.multipass = !one_pass;
+        ne.t.n = (int)n_tab; ne.t.m = (int)m; ne.t.L = L; ne.t.A = A; ne.t.Bh = Bh;
+        ne.multipass = !tab_one_pass;
         ne.lp = lp;
-        const size_t tw_elems = one_pass ? 0 : (size_t)long_czt_table_entries(lp);
-        const size_t elems = (size_t)n + (size_t)L + (size_t)m + tw_elems;
+        const size_t tw_elems = tab_one_pass ? 0 : (size_t)long_czt_table_entries(lp);
+        const size_t elems = (size_t)n_tab + (size_t)L + (size_t)m + tw_elems;
         cudaError_t e = cudaMalloc(&ne.mem, elems * sizeof(float2));
         if (e != cudaSuccess) return cuda_fail(c, e, "CZT tables");
         ne.t.pre = (float2*)ne.mem;
         ne.t.V = ne.t.pre + n;
         ne.t.post = ne.t.V + L;
-        if (!one_pass) {
+        if (!tab_one_pass) {
             ne.tw2 = ne.t.post + m;
             std::vector<float2> host(tw_elems);
             long_fill_tw(lp, host.data());
@@ -561,8 +572,8 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         }
         e = cudaEventCreateWithFlags(&ne.ready, cudaEventDisableTiming);
         if (e != cudaSuccess) { cudaFree(ne.mem); return cuda_fail(c, e, "event"); }
-        e = one_pass ? czt_build_tables(ne.t, c->block_tw + block_twiddle_offset(L), st)
-                     : long_czt_build_tables(lp, ne.t, c->block_tw, ne.tw2, st);
+        e = tab_one_pass ? czt_build_tables(ne.t, c->block_tw + block_twiddle_offset(L), st)
+                         : long_czt_build_tables(lp, ne.t, c->block_tw, ne.tw2, st);
         if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
         if (e != cudaSuccess) {
             cudaFree(ne.mem);
@@ -580,6 +591,23 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     Io io;
     if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
     if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
+    if (segmented) {
+        // W: [traces][segs][M] in chunks of at most ~1 GiB
+        const int64_t per = (int64_t)segs * m * (int64_t)sizeof(float2);
+        const int64_t chunk = std::min<int64_t>(batch, std::max<int64_t>(1, (int64_t(1) << 30) / per));
+        if ((s = ensure_stage(c, 3, (size_t)(chunk * per))) != SPEC_OK) return s;
+        const uint64_t Bs = cycles_to_fixed(step / fs);
+        for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
+            const int64_t nb = std::min(chunk, batch - b0);
+            cudaError_t e = czt_seg_launch(en->t, io.x + b0 * ld_x, nb, n, ld_x, (int)seg_P, segs,
+                                           c->block_tw + block_twiddle_offset(L), (float2*)c->stage[3], st);
+            if (e == cudaSuccess)
+                e = czt_combine_launch((const float2*)c->stage[3], segs, (int)m, nb, A, Bs, seg_P, io.X + b0 * ld_X,
+                                       ld_X, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt segmented launch");
+        }
+        return stage_out_finish(c, X, batch, m, ld_X, st, io);
+    }
     if (en->multipass) {
         float2* work = nullptr;
         int64_t wt = 0;

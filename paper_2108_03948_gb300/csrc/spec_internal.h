@@ -107,6 +107,12 @@ cudaError_t czt_launch2(const CztTables& t, const float* x, int64_t batch, int64
                         const float2* tw, float2* X, int64_t ld_X, cudaStream_t st);
 
 cudaError_t czt_pre_post_launch(const CztTables& t, cudaStream_t st);
+// Segmented chirp-z for N >> M (tables of `t` built for N = seg_len): the
+// segments' spectra into W [batch][segs][M], then their phase-rotated sum.
+cudaError_t czt_seg_launch(const CztTables& t, const float* x, int64_t batch, int64_t n_total, int64_t ld_x,
+                           int seg_len, int segs, const float2* tw, float2* W, cudaStream_t st);
+cudaError_t czt_combine_launch(const float2* W, int segs, int m, int64_t batch, uint64_t A, uint64_t B,
+                               int64_t seg_len, float2* X, int64_t ld_X, cudaStream_t st);
 
 // ---- multi-pass FFT and Bluestein (k_long.cu) ------------------------------
 // P = P1 x 512 points (P = N_FFT/2 for the padded FFT, L for Bluestein);

@@ -1,5 +1,5 @@
-"""Long traces: the multi-pass FFT and Bluestein paths (and the large Zoom
-path) against the FP64 oracle.  Where the oracle can afford every bin the
+"""Long traces: the multi-pass FFT and Bluestein paths, the segmented chirp-z
+(N >> M) and the large Zoom path against the FP64 oracle.  Where the oracle can afford every bin the
 comparison is element by element over the whole spectrum; at the largest
 sizes (262144-sample traces, N_FFT up to 2^24) it is over a fixed sample of
 bins -- both band edges, the ends of the range and a seeded spread -- each
@@ -75,11 +75,19 @@ def test_long_fft_sampled(ctx, S, batch, n, n_fft, kind):
 # ------------------------------------------------------------------- CZT ---
 
 @pytest.mark.parametrize("batch,n,f1,f2,m", [
-    (2, 12000, 0.2e12, 2.5e12, 8000),      # L = 32768, two residues in the column pass
+    # multi-pass Bluestein (M > 8192)
+    (2, 12000, 0.2e12, 2.5e12, 9000),      # L = 32768, two residues in the column pass
     (2, 1000, 0.1e12, 5.0e12, 40000),      # M > N
-    (2, 30000, 0.3e12, 0.31e12, 100),      # M < 512: partial column groups in the last pass
+    (2, 30000, 0.3e12, 0.6e12, 8193),      # just above the segmented limit
+    (2, 5000, 3.0e12, 0.5e12, 20000),      # f2 < f1 (negative step)
+    # segmented (N + M - 1 > 16384, M <= 8192)
+    (2, 12000, 0.2e12, 2.5e12, 8000),      # two segments of a 16384-point Bluestein
+    (2, 30000, 0.3e12, 0.31e12, 100),      # 8192-point segments, ragged last segment
     (2, 20000, 1.0e12, 1.0e12, 1),         # M = 1
     (2, 17000, 3.0e12, 0.5e12, 3000),      # f2 < f1 (negative step)
+    (3, 16385, 0.1e12, 9.9e12, 1),         # one sample past the one-CTA limit
+    (2, 3 * 6145, 0.5e12, 1.5e12, 2048),   # exactly three 8192-point segments
+    (2, 40000, 0.5e12, 1.5e12, 2049),      # 16384-point segments from M = 2049
 ])
 def test_long_czt_full(ctx, S, batch, n, f1, f2, m):
     x = noise(batch, n, m)
@@ -96,6 +104,16 @@ def test_long_czt_workload4_sampled(ctx, S):
     ref = O.czt_bins(x, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m, k)
     assert rel(got[:, k], ref).max() <= TOL
     assert np.isfinite(got).all()
+
+
+def test_segmented_czt_narrow_band_of_long_traces(ctx, S):
+    # the THz use case of N >> M: a 1024-point 0.3-0.4 THz band of
+    # 262144-sample traces, 33 segments of an 8192-point Bluestein
+    cfg = synth.UNIFORM[4]
+    x = synth.batch_traces(4, range(3))
+    got = S.spec_czt(ctx, dev(x), cfg.fs, 0.3e12, 0.4e12, 1024).cpu().numpy()
+    k = sample(1024, 250, 6)
+    assert rel(got[:, k], O.czt_bins(x, cfg.fs, 0.3e12, 0.4e12, 1024, k)).max() <= TOL
 
 
 def test_long_czt_table_cache_and_repeat(ctx, S):
