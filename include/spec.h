@@ -114,7 +114,10 @@ SPEC_API spec_status spec_selftest_wait_timeout(spec_ctx* ctx, int64_t timeout_u
  * The input is real, so the N_FFT/2 + 1 non-redundant bins are written
  * (unnormalised); bin k is frequency k fs / N_FFT.
  *   n      samples per trace, 1 <= n <= n_fft (no truncation)
- *   n_fft  padded length, a power of two, 1 <= n_fft <= 2^24
+ *   n_fft  padded length, 1 <= n_fft <= 2^24; powers of two run the padded
+ *          FFT, any other length (e.g. N_FFT = fs / Delta f for the
+ *          resolution of Eq. 3-5) the chirp-z on the DFT grid (f1 = 0,
+ *          step fs / N_FFT, N_FFT/2 + 1 points), which gives the same bins
  *   fs     sampling frequency (> 0); defines the bin grid only
  *   ld_x >= n, ld_X >= n_fft/2 + 1; x and X must not overlap.
  */

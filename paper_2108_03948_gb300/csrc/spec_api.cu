@@ -468,12 +468,18 @@ spec_status spec_selftest_wait_timeout(spec_ctx* c, int64_t timeout_us, void* st
 spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
                      int64_t n_fft, float* X, int64_t ld_X, void* stream) {
     if (!c) return SPEC_EINVAL;
-    if (n_fft < 1 || n_fft > (int64_t(1) << 24) || !is_pow2(n_fft))
-        return fail(c, SPEC_EINVAL, "n_fft must be a power of two in [1, 2^24]");
+    if (n_fft < 1 || n_fft > (int64_t(1) << 24))
+        return fail(c, SPEC_EINVAL, "n_fft must be in [1, 2^24]");
     const int64_t bins = n_fft / 2 + 1;
     spec_status s = check_common(c, x, batch, n, ld_x, fs, X, bins, ld_X);
     if (s != SPEC_OK) return s;
     if (n_fft < n) return fail(c, SPEC_EINVAL, "n_fft must be >= n (padding never truncates)");
+    if (!is_pow2(n_fft)) {
+        // any other length: the same bins k fs/N_FFT, k = 0 .. N_FFT/2, as a
+        // chirp-z with f1 = 0 and step fs/N_FFT (Eq. 11 on the DFT grid)
+        return spec_czt(c, x, batch, n, ld_x, fs, 0.0, fs * (double)(bins - 1) / (double)n_fft, bins, SPEC_CZT_AUTO,
+                        X, ld_X, stream);
+    }
     FftPlan p;
     LongPlan lp;
     std::string why, why_long;

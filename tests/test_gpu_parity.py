@@ -54,6 +54,12 @@ FFT_CASES = [
 ]
 
 
+# N_FFT not a power of two (the resolution fs/N_FFT of Eq. 3 chosen freely):
+# the chirp-z on the DFT grid; the paper's unpadded 500-sample trace among them
+FFT_CASES += [(3, 500, 500), (2, 500, 1000), (2, 2048, 20000), (3, 1000, 12345), (2, 7, 9), (3, 100, 101),
+              (2, 20000, 40000)]
+
+
 @pytest.mark.parametrize("batch,n,n_fft", FFT_CASES)
 def test_fft_parity(ctx, S, batch, n, n_fft):
     x = traces(batch, n, 100 + n)
@@ -155,7 +161,7 @@ def test_invalid_arguments_return_einval(ctx, S):
     X = torch.zeros((2, 64), dtype=torch.complex64, device="cuda")
     px, pX = x.data_ptr(), X.data_ptr()
     E = S.SPEC_EINVAL
-    assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 1.0, 48, pX, 64, None) == E       # n_fft not pow2
+    assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 1.0, 1 << 25, pX, 64, None) == E  # n_fft above 2^24
     assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 1.0, 32, pX, 64, None) == E       # n_fft < n
     assert lib.spec_fft(ctx.handle, px, 2, 64, 60, 1.0, 64, pX, 64, None) == E       # ld_x < n
     assert lib.spec_fft(ctx.handle, px, 2, 64, 64, 0.0, 64, pX, 64, None) == E       # fs
