@@ -42,7 +42,7 @@ import numpy as np
 
 __all__ = [
     "fft_padded", "fft_padded_bins",
-    "czt", "czt_bins", "czt_grid",
+    "czt", "czt_bins", "czt_grid", "czt_spiral", "czt_spiral_bins",
     "zoom", "zoom_bins", "zoom_grid", "zoom_lout",
     "fft_resolution", "zeros_for_delta", "czt_step", "czt_resolution_eq24",
     "m_for_resolution", "design_lowpass",
@@ -169,6 +169,35 @@ def czt_bins(x, fs: float, f1: float, f2: float, m: int, bins) -> np.ndarray:
 def czt(x, fs: float, f1: float, f2: float, m: int) -> np.ndarray:
     """All M bins of ``czt_bins``: complex128 [batch, M]."""
     return czt_bins(x, fs, f1, f2, m, np.arange(m))
+
+
+def czt_spiral_bins(x, fs: float, f1: float, f2: float, m: int, a0: float, w0: float, bins) -> np.ndarray:
+    """CZT off the unit circle (Eq. 11 with Eq. 16-17): X[k] = sum_n x[n] A^{-n} W^{kn}
+    at the listed k < M, A = a0 e^{j 2 pi f1/fs}, W = w0 e^{-j 2 pi step/fs},
+    i.e. the z-transform on the spiral z_k = A W^{-k}.  The magnitude of
+    A^{-n} W^{kn} is exp(-n ln a0 + k n ln w0) (k n exact in int64); the phase is
+    the unit-circle one.  a0 = w0 = 1 gives ``czt_bins``.
+    """
+    xb = _as_batch(x)
+    nb, n = xb.shape
+    a = f1 / fs
+    b = czt_step(f1, f2, m) / fs
+    la, lw = math.log(a0), math.log(w0)
+    bins = np.asarray(bins, dtype=np.int64)
+    out = np.empty((nb, bins.size), dtype=np.complex128)
+    nn = np.arange(n, dtype=np.int64)
+    chunk = max(1, _CHUNK_ELEMS // max(1, n))
+    for c0 in range(0, bins.size, chunk):
+        kk = bins[c0:c0 + chunk]
+        ang = 2.0 * np.pi * _czt_cycles(nn, kk, a, b)
+        mag = np.exp(-la * nn.astype(np.float64)[:, None] + lw * np.outer(nn, kk).astype(np.float64))
+        out[:, c0:c0 + chunk] = xb @ (mag * np.cos(ang)) - 1j * (xb @ (mag * np.sin(ang)))
+    return out
+
+
+def czt_spiral(x, fs: float, f1: float, f2: float, m: int, a0: float, w0: float) -> np.ndarray:
+    """All M bins of ``czt_spiral_bins``: complex128 [batch, M]."""
+    return czt_spiral_bins(x, fs, f1, f2, m, a0, w0, np.arange(m))
 
 
 # --------------------------------------------------------------------------

@@ -141,6 +141,38 @@ def test_czt_matches_library_czt(n, m, f1, f2):
     assert rel(got, ref) < 1e-9
 
 
+@pytest.mark.parametrize("n,m,f1,f2,a0,w0", [(100, 64, 100.0, 1000.0, 0.98, 1.002),
+                                               (160, 97, 2500.0, 300.0, 1.05, 0.999),
+                                               (77, 1, 250.0, 250.0, 1.1, 0.9995)])
+def test_czt_spiral_matches_library_czt(n, m, f1, f2, a0, w0):
+    # off the unit circle (Eq. 16-17 with A_0, W_0 != 1): scipy's chirp-z on
+    # z_k = a w^{-k} with the complex a = A, w = W
+    fs = 8000.0
+    x = rnd(n, 11, batch=2)
+    step = O.czt_step(f1, f2, m)
+    a = a0 * np.exp(2j * np.pi * f1 / fs)
+    w = w0 * np.exp(-2j * np.pi * step / fs)
+    ref = sps.czt(x, m, w, a, axis=-1)
+    assert rel(O.czt_spiral(x, fs, f1, f2, m, a0, w0), ref) < 1e-9
+
+
+def test_czt_spiral_geometric_closed_form():
+    # x[n] = r^n: X[k] = sum_n (r A^{-1} W^k)^n = (1 - q^N)/(1 - q), q = r W^k / A
+    n, m, fs, f1, f2, a0, w0, r = 300, 50, 10e12, 0.3e12, 2.2e12, 0.995, 1.0004, 0.99
+    x = r ** np.arange(n)
+    step = O.czt_step(f1, f2, m)
+    A = a0 * np.exp(2j * np.pi * f1 / fs)
+    W = w0 * np.exp(-2j * np.pi * step / fs)
+    q = r * W ** np.arange(m) / A
+    ref = (1 - q ** n) / (1 - q)
+    assert rel(O.czt_spiral(x, fs, f1, f2, m, a0, w0)[0], ref) < 1e-11
+
+
+def test_czt_spiral_on_the_unit_circle_is_the_czt():
+    x = rnd(500, 12, batch=2)
+    assert rel(O.czt_spiral(x, 10e12, 0.3e12, 2.9e12, 333, 1.0, 1.0), O.czt(x, 10e12, 0.3e12, 2.9e12, 333)) < 1e-14
+
+
 def test_czt_on_fft_grid_equals_padded_fft_bins():
     n, n_fft, k1, m = 300, 2048, 123, 257
     fs = 20e12
