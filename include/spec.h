@@ -146,6 +146,26 @@ SPEC_API spec_status spec_czt(spec_ctx* ctx, const float* x, int64_t batch, int6
                      int mode, float* X, int64_t ld_X, void* stream);
 
 /*
+ * Chirp-z off the unit circle (Section 2.3, Eq. 11 with Eq. 16-17, A_0 and
+ * W_0 free):
+ *
+ *     X[b][k] = sum_{n<N} x[b][n] A^{-n} W^{k n},  k = 0 .. M-1,
+ *     A = a0 e^{j 2 pi f1/fs},  W = w0 e^{-j 2 pi (f2 - f1)/(fs (M - 1))}
+ *
+ * i.e. the z-transform on the spiral z_k = A W^{-k} (radius a0 w0^{-k});
+ * a0 = w0 = 1 gives spec_czt's bins.  Evaluated as the split-FP16
+ * tensor-core product (SPEC_CZT_GEMM_F16X3) with Z's column k scaled by a
+ * power of two, so that each bin is a direct dot product (Bluestein's
+ * factors w0^{+-n^2/2} leave FP32 range for all but the mildest spirals).
+ *   a0, w0 > 0; SPEC_EUNSUPPORTED when |z_k|^{-n} exceeds 2^100 for some
+ *   k, n, or when Z (2 x 2M x ceil64(N) FP16) exceeds 2 GiB.  Other
+ *   arguments as spec_czt.
+ */
+SPEC_API spec_status spec_czt_spiral(spec_ctx* ctx, const float* x, int64_t batch, int64_t n,
+                            int64_t ld_x, double fs, double f1, double f2, int64_t m,
+                            double a0, double w0, float* X, int64_t ld_X, void* stream);
+
+/*
  * Zoom FFT (Section 2.2, Eq. 6-10): the spectrum around the band centre
  * f_N = (f1 + f2)/2 (Eq. 6) at the FFT's spacing fs/N_FFT:
  *

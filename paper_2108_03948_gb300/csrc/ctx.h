@@ -30,6 +30,8 @@ struct FftEntry {
 struct GemmZEntry {       // cached FP16 split of Z for the GEMM chirp-z
     int64_t n = 0, m = 0;
     uint64_t A = 0, B = 0;
+    double a0 = 1.0, w0 = 1.0;           // contour radius parameters (1, 1: the unit circle)
+    int* col_pow = nullptr;              // off the circle: per-bin column exponents (inside z)
     void* z = nullptr;
     cudaEvent_t ready = nullptr;
     uint64_t last_use = 0;

@@ -150,6 +150,7 @@ struct GemmArgs {
     int64_t tiles;
     int terms;                 // 3 (split) or 1
     const int* row_pow;        // per row: log2 of its scale s
+    const int* col_pow;        // per output bin k: log2 of Z's column scale (spiral contours), or null
     float* out;
     int64_t ld_out;            // floats
     unsigned* status;
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int64_t row = (tile / a.ntn) * BM + q * 32 + lane;
             const int n0 = (int)(tile % a.ntn) * BN;
             const bool live = row < a.rows;
-            const float scale = live ? ldexpf(1.0f, -14 - a.row_pow[row]) : 0.f;
+            const int rp = live ? a.row_pow[row] : 0;
+            const float scale = live ? ldexpf(1.0f, -14 - rp) : 0.f;
             float* orow = a.out + (live ? row : 0) * a.ld_out;
             const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
@@ -306,7 +308,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                             v0 = fmaf(__uint_as_float(r2[j]), 4.8828125e-4f, v0);          // 2^-11
                             v1 = fmaf(__uint_as_float(r2[j + 1]), 4.8828125e-4f, v1);
                         }
-                        if (col < a.cols) *(float2*)(orow + col) = make_float2(v0 * scale, v1 * scale);
+                        if (col < a.cols) {
+                            // off the unit circle Z's column k = col/2 was scaled by 2^-col_pow[k]
+                            const float sc = a.col_pow ? ldexpf(1.0f, -14 - rp + a.col_pow[col >> 1]) : scale;
+                            *(float2*)(orow + col) = make_float2(v0 * sc, v1 * sc);
+                        }
                     }
                 }
             }
@@ -371,6 +377,33 @@ __global__ void k_gemm_build_z(int m, int n, int np, uint64_t A, uint64_t B, __h
     zl[idx] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
 }
 
+// Z off the unit circle (Eq. 16-17 with A_0, W_0 != 1): Z[k][n] = A^{-n} W^{kn},
+// magnitude exp(-n ln A_0 + k n ln W_0), divided by 2^col_pow[k] (the column's
+// largest magnitude rounded up to a power of two), then scaled and split as
+// the unit-circle table.
+__global__ void k_gemm_build_z_spiral(int m, int n, int np, uint64_t A, uint64_t B, double la, double lw,
+                                      const int* col_pow, __half* zh, __half* zl) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)2 * m * np) return;
+    const int c = (int)(idx / np);
+    const int i = (int)(idx % np);
+    const uint64_t k = (uint64_t)(c >> 1);
+    double v = 0.0;
+    if (i < n) {
+        const uint64_t ph = A * (uint64_t)i + B * (k * (uint64_t)i);
+        const double cyc = (double)(int64_t)ph * 5.421010862427522e-20;   // * 2^-64
+        double s, co;
+        sincospi(2.0 * cyc, &s, &co);
+        const double mag = exp(-la * (double)i + lw * (double)(k * (uint64_t)i) -
+                               0.6931471805599453 * (double)col_pow[k]);
+        v = mag * ((c & 1) ? -s : co);
+    }
+    v *= 16384.0;
+    const __half h = __float2half_rn((float)v);
+    zh[idx] = h;
+    zl[idx] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -422,6 +455,17 @@ cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, 
     return cudaGetLastError();
 }
 
+cudaError_t gemm_build_z_spiral(int64_t n, int64_t m, uint64_t A, uint64_t B, double la, double lw,
+                                const int* col_pow, void* z, cudaStream_t st) {
+    const int np = gemm_padded_n(n);
+    __half* zh = (__half*)z;
+    __half* zl = zh + (size_t)2 * m * np;
+    const int64_t total = (int64_t)2 * m * np;
+    k_gemm_build_z_spiral<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((int)m, (int)n, np, A, B, la, lw, col_pow,
+                                                                            zh, zl);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int terms, void* work,
                               cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
@@ -435,7 +479,7 @@ cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t 
 
 cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, const void* z, const void* work,
                             float2* X, int64_t ld_X, unsigned* status, int sms, uint64_t timeout_ns,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int* col_pow) {
     if (batch == 0) return cudaSuccess;
     const int np = gemm_padded_n(n);
     const __half* xh = (const __half*)work;
@@ -456,6 +500,7 @@ cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, cons
     a.tiles = (batch + BM - 1) / BM * a.ntn;
     a.terms = terms;
     a.row_pow = row_pow;
+    a.col_pow = col_pow;
     a.out = (float*)X;
     a.ld_out = 2 * ld_X;
     a.status = status;

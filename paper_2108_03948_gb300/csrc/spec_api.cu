@@ -236,9 +236,24 @@ bool auto_prefers_gemm(const spec_ctx* c, int64_t batch, int64_t n, int64_t m) {
 // (N, M, f1/fs, step/fs), the batch run in chunks whose FP16 split fits a
 // ~1 GiB workspace.
 spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs, double f1,
-                     double f2, int64_t m, int terms, float* X, int64_t ld_X, cudaStream_t st) {
+                     double f2, int64_t m, int terms, float* X, int64_t ld_X, cudaStream_t st, double a0 = 1.0,
+                     double w0 = 1.0) {
     if (gemm_z_bytes(n, m) > (size_t(1) << 31))
         return fail(c, SPEC_EUNSUPPORTED, "GEMM chirp-z: Z above 2 GiB (use SPEC_CZT_BLUESTEIN)");
+    // off the unit circle: column k of Z is scaled by 2^-e_k, e_k the exponent
+    // of its largest magnitude max(1, exp((N-1)(-ln a0 + k ln w0)))
+    const bool spiral = a0 != 1.0 || w0 != 1.0;
+    std::vector<int> col_pow;
+    if (spiral) {
+        col_pow.resize((size_t)m);
+        const double la = std::log(a0), lw = std::log(w0);
+        for (int64_t k = 0; k < m; ++k) {
+            const double lg = (double)(n - 1) * (-la + (double)k * lw) / 0.6931471805599453;
+            if (lg > 100.0)
+                return fail(c, SPEC_EUNSUPPORTED, "spiral chirp-z: the contour's |z_k|^-n exceeds 2^100");
+            col_pow[(size_t)k] = lg > 0.0 ? (int)std::ceil(lg) : 0;
+        }
+    }
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     const double step = m > 1 ? (f2 - f1) / (double)(m - 1) : 0.0;
@@ -246,7 +261,7 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     const uint64_t B = cycles_to_fixed(step / fs);
     GemmZEntry* en = nullptr;
     for (auto& it : c->gemm_z)
-        if (it.n == n && it.m == m && it.A == A && it.B == B) en = &it;
+        if (it.n == n && it.m == m && it.A == A && it.B == B && it.a0 == a0 && it.w0 == w0) en = &it;
     if (!en) {
         if (c->gemm_z.size() >= kCztCacheMax) {
             auto lru = std::min_element(c->gemm_z.begin(), c->gemm_z.end(),
@@ -257,12 +272,19 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
             c->gemm_z.erase(lru);
         }
         GemmZEntry ne;
-        ne.n = n; ne.m = m; ne.A = A; ne.B = B;
-        cudaError_t e = cudaMalloc(&ne.z, gemm_z_bytes(n, m));
+        ne.n = n; ne.m = m; ne.A = A; ne.B = B; ne.a0 = a0; ne.w0 = w0;
+        const size_t zb = (gemm_z_bytes(n, m) + 255) / 256 * 256;
+        cudaError_t e = cudaMalloc(&ne.z, zb + (spiral ? (size_t)m * sizeof(int) : 0));
         if (e != cudaSuccess) return cuda_fail(c, e, "GEMM Z table");
         e = cudaEventCreateWithFlags(&ne.ready, cudaEventDisableTiming);
         if (e != cudaSuccess) { cudaFree(ne.z); return cuda_fail(c, e, "event"); }
-        e = gemm_build_z(n, m, A, B, ne.z, st);
+        if (spiral) {
+            ne.col_pow = (int*)((uint8_t*)ne.z + zb);
+            e = cudaMemcpy(ne.col_pow, col_pow.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess)
+            e = spiral ? gemm_build_z_spiral(n, m, A, B, std::log(a0), std::log(w0), ne.col_pow, ne.z, st)
+                       : gemm_build_z(n, m, A, B, ne.z, st);
         if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
         if (e != cudaSuccess) {
             cudaFree(ne.z);
@@ -293,7 +315,7 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         cudaError_t e = gemm_split_launch(io.x + b0 * ld_x, nb, n, ld_x, terms, c->stage[3], st);
         if (e == cudaSuccess)
             e = gemm_mul_launch(nb, n, m, terms, en->z, c->stage[3], io.X + b0 * ld_X, ld_X, c->status, c->sms,
-                                c->wait_timeout_ns, st);
+                                c->wait_timeout_ns, st, en->col_pow);
         if (e != cudaSuccess) return cuda_fail(c, e, "GEMM chirp-z launch");
     }
     return stage_out_finish(c, X, batch, m, ld_X, st, io);
@@ -628,6 +650,19 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         : czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
     return stage_out_finish(c, X, batch, m, ld_X, st, io);
+}
+
+spec_status spec_czt_spiral(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
+                            double f1, double f2, int64_t m, double a0, double w0, float* X, int64_t ld_X,
+                            void* stream) {
+    if (!c) return SPEC_EINVAL;
+    if (m < 1 || m > (int64_t(1) << 24)) return fail(c, SPEC_EINVAL, "m must be in [1, 2^24]");
+    spec_status s = check_common(c, x, batch, n, ld_x, fs, X, m, ld_X);
+    if (s != SPEC_OK) return s;
+    if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
+    if (!(a0 > 0.0) || !(w0 > 0.0) || !is_finite(a0) || !is_finite(w0))
+        return fail(c, SPEC_EINVAL, "a0 and w0 must be positive and finite");
+    return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, 3, X, ld_X, (cudaStream_t)stream, a0, w0);
 }
 
 spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,

@@ -154,7 +154,10 @@ cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t 
                               cudaStream_t st);
 cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, const void* z, const void* work,
                             float2* X, int64_t ld_X, unsigned* status, int sms, uint64_t timeout_ns,
-                            cudaStream_t st);
+                            cudaStream_t st, const int* col_pow = nullptr);
+// Z off the unit circle; col_pow (device, M ints): log2 of each column's scale.
+cudaError_t gemm_build_z_spiral(int64_t n, int64_t m, uint64_t A, uint64_t B, double la, double lw,
+                                const int* col_pow, void* z, cudaStream_t st);
 cudaError_t wait_selftest_launch(unsigned* status, uint64_t timeout_ns, cudaStream_t st);
 
 // ---- Zoom FFT (k_zoom.cu) -------------------------------------------------

@@ -27,7 +27,8 @@ _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "
 
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
            "spec_selftest_wait_timeout", "spec_measure_fp32_peak",
-           "spec_fft", "spec_czt", "spec_zoom", "spec_czt_static", "spec_ragged", "spec_ragged_launches",
+           "spec_fft", "spec_czt", "spec_czt_spiral", "spec_zoom", "spec_czt_static", "spec_ragged",
+           "spec_ragged_launches",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
 
 SPEC_KIND_FFT, SPEC_KIND_CZT, SPEC_KIND_ZOOM = 0, 1, 2
@@ -74,6 +75,8 @@ def lib():
     L.spec_fft.restype = C.c_int
     L.spec_czt.argtypes = [vp, fp, i64, i64, i64, dbl, dbl, dbl, i64, C.c_int, fp, i64, vp]
     L.spec_czt.restype = C.c_int
+    L.spec_czt_spiral.argtypes = [vp, fp, i64, i64, i64, dbl, dbl, dbl, i64, dbl, dbl, fp, i64, vp]
+    L.spec_czt_spiral.restype = C.c_int
     L.spec_zoom.argtypes = [vp, fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, i64, fp, i64, vp]
     L.spec_zoom.restype = C.c_int
     L.spec_ragged.argtypes = [vp, C.c_int, C.POINTER(spec_desc), i64, dbl, fp, fp, fp, vp]
@@ -207,6 +210,18 @@ def spec_czt(ctx: Context, x, fs: float, f1: float, f2: float, m: int, n: int | 
     o, po, ld_o = _out(dev, keep, batch, int(m), out)
     ctx.check(lib().spec_czt(ctx.handle, px, batch, n, ld_x, float(fs), float(f1), float(f2), int(m),
                              int(mode), po, ld_o, st if stream is None else stream))
+    return o
+
+
+def spec_czt_spiral(ctx: Context, x, fs: float, f1: float, f2: float, m: int, a0: float, w0: float,
+                    n: int | None = None, out=None, stream=None):
+    """Chirp-z on the spiral z_k = A W^{-k}, A = a0 e^{j2pi f1/fs}, W = w0 e^{-j2pi step/fs}
+    (Section 2.3, Eq. 11 with Eq. 16-17)."""
+    keep, px, batch, ld_x, dev, st = _rows(x)
+    n = keep.shape[1] if n is None else int(n)
+    o, po, ld_o = _out(dev, keep, batch, int(m), out)
+    ctx.check(lib().spec_czt_spiral(ctx.handle, px, batch, n, ld_x, float(fs), float(f1), float(f2), int(m),
+                                    float(a0), float(w0), po, ld_o, st if stream is None else stream))
     return o
 
 

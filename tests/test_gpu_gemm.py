@@ -154,3 +154,38 @@ def test_gemm_large_batch_matches_small_calls(ctx, S):
     b = big.view(48, 1024, 512)
     for r in (0, 17, 33, 47):
         assert torch.equal(torch.view_as_real(b[r]), torch.view_as_real(one))
+
+
+# ------------------------------------------------------ off the unit circle
+
+SPIRALS = [
+    (4, 1024, 0.8e12, 1.2e12, 512, 0.999, 1.0001),
+    (3, 1000, 0.2e12, 2.5e12, 300, 1.01, 0.9999),
+    (5, 500, 0.1e12, 5.0e12, 100, 0.98, 1.001),        # column scales up to ~2^86
+    (129, 77, 3.0e12, 0.5e12, 33, 1.002, 0.998),       # descending band, ragged tiles
+]
+
+
+@pytest.mark.parametrize("batch,n,f1,f2,m,a0,w0", SPIRALS)
+def test_spiral_czt_parity(ctx, S, batch, n, f1, f2, m, a0, w0):
+    x = noise(batch, n, n + m + 1)
+    got = S.spec_czt_spiral(ctx, dev(x), FS, f1, f2, m, a0, w0).cpu().numpy()
+    assert rel(got, O.czt_spiral(x, FS, f1, f2, m, a0, w0)).max() <= TOL
+
+
+def test_spiral_czt_on_the_unit_circle_is_the_gemm_czt(ctx, S):
+    x = dev(noise(300, 1024, 21))
+    a = S.spec_czt_spiral(ctx, x, FS, 0.8e12, 1.2e12, 512, 1.0, 1.0)
+    b = S.spec_czt(ctx, x, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3)
+    assert torch.equal(torch.view_as_real(a), torch.view_as_real(b))
+
+
+def test_spiral_czt_rejections(ctx, S):
+    lib = S.lib()
+    x = torch.zeros((2, 1000), device="cuda")
+    X = torch.zeros((2, 64), dtype=torch.complex64, device="cuda")
+    args = (ctx.handle, x.data_ptr(), 2, 1000, 1000, FS, 0.1e12, 1.0e12, 64)
+    assert lib.spec_czt_spiral(*args, 0.0, 1.0, X.data_ptr(), 64, None) == S.SPEC_EINVAL
+    assert lib.spec_czt_spiral(*args, 1.0, -1.0, X.data_ptr(), 64, None) == S.SPEC_EINVAL
+    assert lib.spec_czt_spiral(*args, 0.5, 1.0, X.data_ptr(), 64, None) == S.SPEC_EUNSUPPORTED   # 2^999
+    assert np.all(X.cpu().numpy() == 0)
