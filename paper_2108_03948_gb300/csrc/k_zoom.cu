@@ -34,10 +34,42 @@ struct ZoomArgs {
     const RaggedItem* items;   // ragged batch: per-trace placement and parameters (else null)
 };
 
-constexpr int kZoomGroup = 4;   // outputs per thread per pass over the taps
+constexpr int kZoomGroup = 4;   // outputs per thread per pass over the taps (at most)
+
+// FIR + decimate of one trace: thread t computes the G outputs
+// m = m0 + u T (u < G) per pass over the taps, each tap read once per G
+// multiply-add pairs, and stores u[m] e^{-j w m D} into s (padded index).
+template <int G, int T>
+__device__ __forceinline__ void zoom_fir(const float4* tap, const float* xs, float2* s, int n_taps, int lout,
+                                         uint64_t Cn, int D, int t) {
+    for (int m0 = t; m0 < lout; m0 += G * T) {
+        float re[G], im[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) re[u] = im[u] = 0.f;
+        const float* xm = xs + m0;
+        for (int k = 0; k < n_taps; ++k) {
+            const float4 g = tap[k];
+            const float* xk = xm + __float_as_int(g.z);
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const float xv = xk[u * T];
+                re[u] = fmaf(g.x, xv, re[u]);
+                im[u] = fmaf(g.y, xv, im[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int m = m0 + u * T;
+            if (m < lout) {
+                const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
+                s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
+            }
+        }
+    }
+}
 
 template <int K>
-__global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
+__global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 1024 ? 1 : (FFTShape<K>::T >= 32 ? 1024 / FFTShape<K>::T : 32)) k_zoom(ZoomArgs a) {
     using FFT = BlockFFT<K, false>;
     constexpr int E = FFT::E, T = FFT::T;
     extern __shared__ float4 smem4[];
@@ -95,30 +127,13 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom(ZoomArgs a) {
     }
     __syncthreads();
 
-    // FIR + decimate: groups of four outputs m = t + T (4 g + u)
-    for (int m0 = t; m0 < lout; m0 += kZoomGroup * T) {
-        float re[kZoomGroup], im[kZoomGroup];
-#pragma unroll
-        for (int u = 0; u < kZoomGroup; ++u) re[u] = im[u] = 0.f;
-        const float* xm = xs + m0;
-        for (int k = 0; k < n_taps; ++k) {
-            const float4 g = tap[k];
-            const float* xk = xm + __float_as_int(g.z);
-#pragma unroll
-            for (int u = 0; u < kZoomGroup; ++u) {
-                const float xv = xk[u * T];
-                re[u] = fmaf(g.x, xv, re[u]);
-                im[u] = fmaf(g.y, xv, im[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kZoomGroup; ++u) {
-            const int m = m0 + u * T;
-            if (m < lout) {
-                const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
-                s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
-            }
-        }
+    // FIR + decimate: groups of G outputs m = t + T (G g + u), G just large
+    // enough to cover L_out in one pass where possible (no idle slots)
+    switch (min(kZoomGroup, (lout + T - 1) / T)) {
+        case 1: zoom_fir<1, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
+        case 2: zoom_fir<2, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
+        case 3: zoom_fir<3, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
+        default: zoom_fir<4, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
     }
     __syncthreads();
     float2 v[E];
