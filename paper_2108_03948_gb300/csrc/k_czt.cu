@@ -72,8 +72,10 @@ struct BluesteinArgs {
     int64_t n_total;           // segmented: samples per trace N
 };
 
+// Up to L = 4096: 256 threads (one or more traces) at four CTAs per SM, i.e.
+// 64 registers, which this kernel fits without spills.
 template <int L>
-__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, FFTShape<L>::T > 256 ? 1 : 2) k_czt_bluestein(BluesteinArgs a) {
+__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, FFTShape<L>::T > 256 ? 1 : 4) k_czt_bluestein(BluesteinArgs a) {
     using Fw = BlockFFT<L, false>;
     using Iv = BlockFFT<L, true>;
     constexpr int E = Fw::E, T = Fw::T;

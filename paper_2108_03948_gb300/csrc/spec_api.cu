@@ -584,15 +584,16 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         ne.t.n = (int)n_tab; ne.t.m = (int)m; ne.t.L = L; ne.t.A = A; ne.t.Bh = Bh;
         ne.multipass = !tab_one_pass;
         ne.lp = lp;
+        // one allocation: pre[n_tab] | V[L] | post[M] | multi-pass twiddles
         const size_t tw_elems = tab_one_pass ? 0 : (size_t)long_czt_table_entries(lp);
-        const size_t elems = (size_t)n_tab + (size_t)L + (size_t)m + tw_elems;
-        cudaError_t e = cudaMalloc(&ne.mem, elems * sizeof(float2));
+        const size_t off_V = (size_t)n_tab, off_post = off_V + (size_t)L, off_tw = off_post + (size_t)m;
+        cudaError_t e = cudaMalloc(&ne.mem, (off_tw + tw_elems) * sizeof(float2));
         if (e != cudaSuccess) return cuda_fail(c, e, "CZT tables");
         ne.t.pre = (float2*)ne.mem;
-        ne.t.V = ne.t.pre + n;
-        ne.t.post = ne.t.V + L;
+        ne.t.V = ne.t.pre + off_V;
+        ne.t.post = ne.t.pre + off_post;
         if (!tab_one_pass) {
-            ne.tw2 = ne.t.post + m;
+            ne.tw2 = ne.t.pre + off_tw;
             std::vector<float2> host(tw_elems);
             long_fill_tw(lp, host.data());
             e = cudaMemcpy(ne.tw2, host.data(), tw_elems * sizeof(float2), cudaMemcpyHostToDevice);
