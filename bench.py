@@ -96,6 +96,35 @@ def measured_tensor_peak():
     return 1900.0, "fallback 1.9 PFLOP/s bf16 burst (of fallback)"
 
 
+def host_link_gbs(dev, nbytes=256 << 20, reps=5):
+    """Pinned host <-> device copy bandwidth (GB/s): upload alone, download
+    alone, and both at once on two streams (sum of the two directions) --
+    the ceiling of the end-to-end path, which moves every step's inputs and
+    spectra across this link."""
+    import torch
+    h_src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_dst = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(up, down):
+        ts = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            if up:
+                with torch.cuda.stream(s_up):
+                    d_a.copy_(h_src, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s_down):
+                    h_dst.copy_(d_b, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t0)
+        return (int(up) + int(down)) * nbytes / statistics.median(ts[1:]) / 1e9
+    return {"h2d_gbs": timed(True, False), "d2h_gbs": timed(False, True), "duplex_gbs": timed(True, True)}
+
+
 def csrc_digest():
     """Digest of the kernel sources: stored traffic counters are valid only
     for the sources they were taken from."""
@@ -548,13 +577,21 @@ class Ragged:
         hs = {k: torch.empty(v.shape, dtype=torch.complex64).pin_memory() for k, v in self.out.items()}
         parts = self.parts()
 
+        side = torch.cuda.Stream()
+        done = {k: torch.cuda.Event() for k in self.out}
+
         def step():
+            main = torch.cuda.current_stream()
             self.xd.copy_(xh, non_blocking=True)
             self.taps_d.copy_(th, non_blocking=True)
-            for _, f in parts:
+            for k, f in parts:
                 f()
-            for k, v in self.out.items():
-                hs[k].copy_(v, non_blocking=True)
+                # each transform's spectra go down while the next one computes
+                done[k].record(main)
+                side.wait_event(done[k])
+                with torch.cuda.stream(side):
+                    hs[k].copy_(self.out[k], non_blocking=True)
+            main.wait_stream(side)          # the next step overwrites the pools
 
         def check():
             torch.cuda.synchronize()
@@ -648,6 +685,12 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_val = job_throughput(bins_step, e2e_steps, world, e2e_s)
     e2e_diff = e2e_check()
+    link = host_link_gbs(dev)
+    # copy-bound step time: each direction at its own measured rate, the two
+    # overlapping (bounded below by the duplex rate on the sum)
+    copy_ms = 1e3 * max(h2d / (link["h2d_gbs"] * 1e9), d2h / (link["d2h_gbs"] * 1e9),
+                        (h2d + d2h) / (link["duplex_gbs"] * 1e9))
+    e2e_ms = 1e3 * e2e_s / e2e_steps
 
     if rank != 0:
         ctx.close()
@@ -729,7 +772,9 @@ def run_ours(args):
         "kernels": kern,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps, "max_abs_diff_vs_device_path": e2e_diff},
+                "steps": e2e_steps, "max_abs_diff_vs_device_path": e2e_diff, "ms_per_step": e2e_ms,
+                "link": {k: round(v, 1) for k, v in link.items()}, "copy_bound_ms": copy_ms,
+                "frac_of_copy_bound": copy_ms / e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "library_comparison": lib_cmp,

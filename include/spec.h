@@ -11,7 +11,10 @@
  *       (re, im) interleaved; ld_X counts complex elements.
  *   x and X may be device pointers (async on `stream`, no host sync) or host
  *   pointers (pageable or pinned): host buffers are staged through
- *   library-owned device memory and the call returns once X holds the result.
+ *   library-owned device memory in chunks of traces, the upload of one chunk,
+ *   the transform of the previous one (on `stream`) and the download of the
+ *   one before overlapping (fully so with pinned memory), and the call
+ *   returns once X holds the result.
  *   The caller owns x, X and the taps; the library owns only what sits in the
  *   context (tables, caches, staging buffers).
  *   `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).

@@ -54,8 +54,12 @@ struct spec_ctx {
     uint64_t wait_timeout_ns = 1000000000ull;
     std::vector<RaggedPlan*> ragged;     // cached ragged-batch plans (graph + per-trace tables)
     uint64_t tick = 0;
-    void* stage[4] = {nullptr, nullptr, nullptr, nullptr};   // x, X, taps, workspace
+    void* stage[4] = {nullptr, nullptr, nullptr, nullptr};   // x, X (two host-buffer chunks each), taps, workspace
     size_t stage_bytes[4] = {0, 0, 0, 0};
+    cudaStream_t copy[2] = {nullptr, nullptr};  // host-buffer uploads, downloads (created on first use)
+    cudaEvent_t ev_in[2] = {nullptr, nullptr};   // per staging slot: upload done,
+    cudaEvent_t ev_tr[2] = {nullptr, nullptr};   // transform done,
+    cudaEvent_t ev_out[2] = {nullptr, nullptr};  // download done
 };
 
 namespace spec {

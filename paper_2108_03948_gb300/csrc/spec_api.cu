@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -111,9 +112,14 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 
 bool is_finite(double v) { return std::isfinite(v); }
 
+// Staging slots grow only; a buffer being replaced may still be in use by
+// work queued on any stream, so the device drains first.
 spec_status ensure_stage(spec_ctx* c, int slot, size_t bytes) {
     if (c->stage_bytes[slot] >= bytes) return SPEC_OK;
-    if (c->stage[slot]) cudaFree(c->stage[slot]);
+    if (c->stage[slot]) {
+        cudaDeviceSynchronize();
+        cudaFree(c->stage[slot]);
+    }
     c->stage[slot] = nullptr;
     c->stage_bytes[slot] = 0;
     cudaError_t e = cudaMalloc(&c->stage[slot], bytes);
@@ -122,55 +128,106 @@ spec_status ensure_stage(spec_ctx* c, int slot, size_t bytes) {
     return SPEC_OK;
 }
 
-// Where x (input rows) and X (output rows) live; host buffers get device
-// staging and a synchronous copy-back.
-struct Io {
-    const float* x = nullptr;
-    float2* X = nullptr;
-    bool x_host = false, X_host = false;
-};
+// Host buffers.  A call whose x or X is host memory runs the batch in chunks
+// of traces through two device staging slots per direction, so that the
+// upload of chunk i+1 (copy stream 0), the transform of chunk i (the caller's
+// stream) and the download of chunk i-1 (copy stream 1) overlap.  Events
+// order the reuse of the slots:
+//   upload i     waits for transform i-2 (which read its input slot),
+//   transform i  waits for upload i and for download i-2 (its output slot),
+//   download i   waits for transform i.
+// The call returns once X holds the result, so the caller may reuse the host
+// buffers at once.  `fn` runs the transform of one chunk on device pointers.
+using ChunkFn = std::function<spec_status(const float* xd, int64_t ld_xd, float2* Xd, int64_t ld_Xd, int64_t nb)>;
 
-spec_status stage_in(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x,
-                     cudaStream_t st, Io* io) {
-    io->x_host = !is_device_ptr(x);
-    if (!io->x_host) {
-        io->x = x;
-        return SPEC_OK;
+// Traces per chunk: one chunk below 16 MiB of host traffic; otherwise 4 - 64
+// chunks of about 32 MiB each, rounded up to a multiple of 64 traces.  No
+// chunk holds a single trace unless the batch does (the two-trace kernels
+// then see the same pairs as in a device-pointer call).
+int64_t pipeline_chunk(int64_t batch, int64_t bytes_per_trace) {
+    const double total = (double)batch * (double)bytes_per_trace;
+    if (total < 16.0 * 1048576.0) return std::max<int64_t>(1, batch);
+    const int64_t parts = (int64_t)std::min(64.0, std::max(4.0, total / (32.0 * 1048576.0)));
+    int64_t chunk = (batch + parts - 1) / parts;
+    if (chunk > 64) chunk = (chunk + 63) / 64 * 64;
+    while (chunk < batch && batch % chunk == 1) chunk += 2;
+    return std::max<int64_t>(1, std::min(chunk, batch));
+}
+
+spec_status ensure_copy_streams(spec_ctx* c) {
+    if (c->copy[0]) return SPEC_OK;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&c->copy[k], cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_tr[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming);
     }
-    const size_t bytes = (size_t)((batch - 1) * ld_x + n) * sizeof(float);
-    spec_status s = ensure_stage(c, 0, bytes);
-    if (s != SPEC_OK) return s;
-    cudaError_t e = cudaMemcpy2DAsync(c->stage[0], ld_x * sizeof(float), x, ld_x * sizeof(float),
-                                      n * sizeof(float), batch, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy of x");
-    io->x = (const float*)c->stage[0];
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy streams");
     return SPEC_OK;
 }
 
-spec_status stage_out_alloc(spec_ctx* c, float* X, int64_t batch, int64_t bins, int64_t ld_X, Io* io) {
-    io->X_host = !is_device_ptr(X);
-    if (!io->X_host) {
-        io->X = reinterpret_cast<float2*>(X);
-        return SPEC_OK;
+spec_status host_pipeline(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, float* X,
+                          int64_t bins, int64_t ld_X, cudaStream_t st, const ChunkFn& fn) {
+    const bool xh = !is_device_ptr(x), Xh = !is_device_ptr(X);
+    const int64_t chunk = pipeline_chunk(batch, (xh ? n * 4 : 0) + (Xh ? bins * 8 : 0));
+    spec_status s = SPEC_OK;
+    if ((s = ensure_copy_streams(c)) != SPEC_OK) return s;
+    if (xh && (s = ensure_stage(c, 0, 2 * (size_t)chunk * (size_t)n * sizeof(float))) != SPEC_OK) return s;
+    if (Xh && (s = ensure_stage(c, 1, 2 * (size_t)chunk * (size_t)bins * sizeof(float2))) != SPEC_OK) return s;
+    cudaStream_t up = c->copy[0], down = c->copy[1];
+    float2* X2 = reinterpret_cast<float2*>(X);
+    const int64_t nch = (batch + chunk - 1) / chunk;
+    cudaError_t e = cudaSuccess;
+    auto download = [&](int64_t i) {
+        const int sl = (int)(i & 1);
+        const int64_t b0 = i * chunk, nb = std::min(chunk, batch - b0);
+        e = cudaStreamWaitEvent(down, c->ev_tr[sl], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(X2 + b0 * ld_X, ld_X * sizeof(float2), (float2*)c->stage[1] + sl * chunk * bins,
+                                  bins * sizeof(float2), bins * sizeof(float2), nb, cudaMemcpyDeviceToHost, down);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[sl], down);
+    };
+    for (int64_t i = 0; i < nch; ++i) {
+        const int sl = (int)(i & 1);
+        const int64_t b0 = i * chunk, nb = std::min(chunk, batch - b0);
+        const float* xd = x + b0 * ld_x;
+        int64_t ld_xd = ld_x;
+        if (xh) {
+            float* slot = (float*)c->stage[0] + sl * chunk * n;
+            e = cudaStreamWaitEvent(up, c->ev_tr[sl], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(slot, n * sizeof(float), xd, ld_x * sizeof(float), n * sizeof(float), nb,
+                                      cudaMemcpyHostToDevice, up);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[sl], up);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_in[sl], 0);
+            xd = slot;
+            ld_xd = n;
+        }
+        float2* Xd = X2 + b0 * ld_X;
+        int64_t ld_Xd = ld_X;
+        if (Xh) {
+            Xd = (float2*)c->stage[1] + sl * chunk * bins;
+            ld_Xd = bins;
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_out[sl], 0);
+        }
+        if (e != cudaSuccess) break;
+        if ((s = fn(xd, ld_xd, Xd, ld_Xd, nb)) != SPEC_OK) break;
+        if ((e = cudaEventRecord(c->ev_tr[sl], st)) != cudaSuccess) break;
+        if (Xh && i > 0) download(i - 1);
+        if (e != cudaSuccess) break;
     }
-    const size_t bytes = (size_t)((batch - 1) * ld_X + bins) * sizeof(float2);
-    spec_status s = ensure_stage(c, 1, bytes);
+    if (e == cudaSuccess && s == SPEC_OK && Xh) {
+        download(nch - 1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_out[(nch - 1) & 1], 0);
+    }
+    // whatever happened, nothing may still be copying from or to the
+    // caller's buffers when the call returns
+    const cudaError_t e1 = cudaStreamSynchronize(up), e2 = cudaStreamSynchronize(down);
+    const cudaError_t e3 = cudaStreamSynchronize(st);
     if (s != SPEC_OK) return s;
-    io->X = (float2*)c->stage[1];
-    return SPEC_OK;
-}
-
-spec_status stage_out_finish(spec_ctx* c, float* X, int64_t batch, int64_t bins, int64_t ld_X,
-                             cudaStream_t st, const Io& io) {
-    if (!io.X_host && !io.x_host) return SPEC_OK;
-    if (io.X_host) {
-        cudaError_t e = cudaMemcpy2DAsync(X, ld_X * sizeof(float2), io.X, ld_X * sizeof(float2),
-                                          bins * sizeof(float2), batch, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy of X");
-    }
-    // host buffers: the caller may reuse them as soon as the call returns
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "transform");
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-buffer transform");
     return SPEC_OK;
 }
 
@@ -298,10 +355,8 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         if (e != cudaSuccess) return cuda_fail(c, e, "table wait");
     }
     en->last_use = ++c->tick;
-    Io io;
     spec_status s;
-    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
-    if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
+    float2* X2 = reinterpret_cast<float2*>(X);
     // The FP16 split then the product, in chunks only when the workspace
     // would exceed 512 MiB (one product over the whole batch keeps the tile
     // waves full; smaller products measured slower, even with the split of
@@ -312,13 +367,13 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if ((s = ensure_stage(c, 3, gemm_work_bytes(chunk, n))) != SPEC_OK) return s;
     for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
         const int64_t nb = std::min(chunk, batch - b0);
-        cudaError_t e = gemm_split_launch(io.x + b0 * ld_x, nb, n, ld_x, terms, c->stage[3], st);
+        cudaError_t e = gemm_split_launch(x + b0 * ld_x, nb, n, ld_x, terms, c->stage[3], st);
         if (e == cudaSuccess)
-            e = gemm_mul_launch(nb, n, m, terms, en->z, c->stage[3], io.X + b0 * ld_X, ld_X, c->status, c->sms,
+            e = gemm_mul_launch(nb, n, m, terms, en->z, c->stage[3], X2 + b0 * ld_X, ld_X, c->status, c->sms,
                                 c->wait_timeout_ns, st, en->col_pow);
         if (e != cudaSuccess) return cuda_fail(c, e, "GEMM chirp-z launch");
     }
-    return stage_out_finish(c, X, batch, m, ld_X, st, io);
+    return SPEC_OK;
 }
 
 // Twiddle table of the multi-pass transforms (period 2^logTw), cached.
@@ -454,6 +509,12 @@ void spec_ctx_destroy(spec_ctx* c) {
         if (c->block_tw) cudaFree(c->block_tw);
         for (int i = 0; i < 4; ++i)
             if (c->stage[i]) cudaFree(c->stage[i]);
+        for (int k = 0; k < 2; ++k) {
+            if (c->copy[k]) cudaStreamDestroy(c->copy[k]);
+            if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+            if (c->ev_tr[k]) cudaEventDestroy(c->ev_tr[k]);
+            if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+        }
         cudaGetLastError();
     }
     delete c;
@@ -511,25 +572,28 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    Io io;
-    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
-    if ((s = stage_out_alloc(c, X, batch, bins, ld_X, &io)) != SPEC_OK) return s;
+    if (!is_device_ptr(x) || !is_device_ptr(X))
+        return host_pipeline(c, x, batch, n, ld_x, X, bins, ld_X, st,
+                             [&](const float* xd, int64_t ld_xd, float2* Xd, int64_t ld_Xd, int64_t nb) {
+                                 return spec_fft(c, xd, nb, n, ld_xd, fs, n_fft, (float*)Xd, ld_Xd, stream);
+                             });
+    float2* X2 = reinterpret_cast<float2*>(X);
     if (!one_pass) {
         const float2* tw = nullptr;
         float2* work = nullptr;
         int64_t wt = 0;
         if ((s = long_table(c, lp, &tw)) != SPEC_OK) return s;
         if ((s = long_work(c, lp, batch, &work, &wt)) != SPEC_OK) return s;
-        cudaError_t e = long_fft_launch(lp, io.x, batch, (int)n, ld_x, c->block_tw, tw, work, wt, io.X, ld_X, st);
+        cudaError_t e = long_fft_launch(lp, x, batch, (int)n, ld_x, c->block_tw, tw, work, wt, X2, ld_X, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft multi-pass launch");
-        return stage_out_finish(c, X, batch, bins, ld_X, st, io);
+        return SPEC_OK;
     }
     const float2* tab = nullptr;
     if (p.H > 0 && (s = plan_table(c, 0, p, &tab)) != SPEC_OK) return s;
-    cudaError_t e = fft_launch(p, io.x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ, p.emax), tab,
-                               io.X, ld_X, st, c->lanes);
+    cudaError_t e = fft_launch(p, x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ, p.emax), tab,
+                               X2, ld_X, st, c->lanes);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
-    return stage_out_finish(c, X, batch, bins, ld_X, st, io);
+    return SPEC_OK;
 }
 
 spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
@@ -540,13 +604,16 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if (s != SPEC_OK) return s;
     if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
     if (mode < SPEC_CZT_AUTO || mode > SPEC_CZT_GEMM_F16X1) return fail(c, SPEC_EINVAL, "unknown CZT mode");
-    if (mode == SPEC_CZT_AUTO && auto_prefers_gemm(c, batch, n, m)) mode = SPEC_CZT_GEMM_F16X3;
-    if (mode == SPEC_CZT_GEMM_F16X3 || mode == SPEC_CZT_GEMM_F16X1)
-        return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, mode == SPEC_CZT_GEMM_F16X3 ? 3 : 1, X, ld_X,
-                        (cudaStream_t)stream);
+    // AUTO is decided on the whole batch (chunks of a host-buffer call then
+    // all run the same arithmetic)
+    if (mode == SPEC_CZT_AUTO)
+        mode = auto_prefers_gemm(c, batch, n, m) ? SPEC_CZT_GEMM_F16X3 : SPEC_CZT_BLUESTEIN;
+    const bool gemm = mode == SPEC_CZT_GEMM_F16X3 || mode == SPEC_CZT_GEMM_F16X1;
+    if (gemm && gemm_z_bytes(n, m) > (size_t(1) << 31))
+        return fail(c, SPEC_EUNSUPPORTED, "GEMM chirp-z: Z above 2 GiB (use SPEC_CZT_BLUESTEIN)");
     std::string why, why_long;
     LongPlan lp;
-    const bool one_pass = czt_supported(n, m, &why);
+    const bool one_pass = gemm || czt_supported(n, m, &why);
     // N + M - 1 beyond one CTA: with M <= 8192 the trace is cut into segments
     // of P = L' - M + 1 samples that each fit a one-CTA Bluestein of length L'
     // (Section 2.3's sum split over n); otherwise the multi-pass Bluestein.
@@ -559,6 +626,15 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if (batch == 0) return SPEC_OK;
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (!is_device_ptr(x) || !is_device_ptr(X))
+        return host_pipeline(c, x, batch, n, ld_x, X, m, ld_X, st,
+                             [&](const float* xd, int64_t ld_xd, float2* Xd, int64_t ld_Xd, int64_t nb) {
+                                 return spec_czt(c, xd, nb, n, ld_xd, fs, f1, f2, m, mode, (float*)Xd, ld_Xd,
+                                                 stream);
+                             });
+    if (gemm)
+        return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, mode == SPEC_CZT_GEMM_F16X3 ? 3 : 1, X, ld_X, st);
+    float2* X2 = reinterpret_cast<float2*>(X);
 
     // Bluestein tables for (N, M, f1/fs, step/fs), cached (for a segmented
     // transform: the tables of one segment, N = P)
@@ -617,9 +693,6 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     }
     en->last_use = ++c->tick;
 
-    Io io;
-    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
-    if ((s = stage_out_alloc(c, X, batch, m, ld_X, &io)) != SPEC_OK) return s;
     if (segmented) {
         // W: [traces][segs][M] in chunks of at most ~1 GiB
         const int64_t per = (int64_t)segs * m * (int64_t)sizeof(float2);
@@ -628,29 +701,29 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         const uint64_t Bs = cycles_to_fixed(step / fs);
         for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
             const int64_t nb = std::min(chunk, batch - b0);
-            cudaError_t e = czt_seg_launch(en->t, io.x + b0 * ld_x, nb, n, ld_x, (int)seg_P, segs,
+            cudaError_t e = czt_seg_launch(en->t, x + b0 * ld_x, nb, n, ld_x, (int)seg_P, segs,
                                            c->block_tw + block_twiddle_offset(L), (float2*)c->stage[3], st);
             if (e == cudaSuccess)
-                e = czt_combine_launch((const float2*)c->stage[3], segs, (int)m, nb, A, Bs, seg_P, io.X + b0 * ld_X,
+                e = czt_combine_launch((const float2*)c->stage[3], segs, (int)m, nb, A, Bs, seg_P, X2 + b0 * ld_X,
                                        ld_X, st);
             if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt segmented launch");
         }
-        return stage_out_finish(c, X, batch, m, ld_X, st, io);
+        return SPEC_OK;
     }
     if (en->multipass) {
         float2* work = nullptr;
         int64_t wt = 0;
         if ((s = long_work(c, en->lp, batch, &work, &wt)) != SPEC_OK) return s;
-        cudaError_t e = long_czt_launch(en->lp, en->t, en->tw2, io.x, batch, ld_x, c->block_tw, work, wt, io.X,
+        cudaError_t e = long_czt_launch(en->lp, en->t, en->tw2, x, batch, ld_x, c->block_tw, work, wt, X2,
                                         ld_X, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt multi-pass launch");
-        return stage_out_finish(c, X, batch, m, ld_X, st, io);
+        return SPEC_OK;
     }
     cudaError_t e = (czt_dual_ok(L) && c->lanes == 2)
-        ? czt_launch2(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st)
-        : czt_launch(en->t, io.x, batch, ld_x, c->block_tw + block_twiddle_offset(L), io.X, ld_X, st);
+        ? czt_launch2(en->t, x, batch, ld_x, c->block_tw + block_twiddle_offset(L), X2, ld_X, st)
+        : czt_launch(en->t, x, batch, ld_x, c->block_tw + block_twiddle_offset(L), X2, ld_X, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
-    return stage_out_finish(c, X, batch, m, ld_X, st, io);
+    return SPEC_OK;
 }
 
 spec_status spec_czt_spiral(spec_ctx* c, const float* x, int64_t batch, int64_t n, int64_t ld_x, double fs,
@@ -663,6 +736,16 @@ spec_status spec_czt_spiral(spec_ctx* c, const float* x, int64_t batch, int64_t 
     if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
     if (!(a0 > 0.0) || !(w0 > 0.0) || !is_finite(a0) || !is_finite(w0))
         return fail(c, SPEC_EINVAL, "a0 and w0 must be positive and finite");
+    if (batch > 0 && (!is_device_ptr(x) || !is_device_ptr(X))) {
+        // the contour's limits are checked once, before any copy
+        if ((s = czt_gemm(c, x, 0, n, ld_x, fs, f1, f2, m, 3, X, ld_X, nullptr, a0, w0)) != SPEC_OK) return s;
+        DeviceGuard g(c->device);
+        return host_pipeline(c, x, batch, n, ld_x, X, m, ld_X, (cudaStream_t)stream,
+                             [&](const float* xd, int64_t ld_xd, float2* Xd, int64_t ld_Xd, int64_t nb) {
+                                 return spec_czt_spiral(c, xd, nb, n, ld_xd, fs, f1, f2, m, a0, w0, (float*)Xd,
+                                                        ld_Xd, stream);
+                             });
+    }
     return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, 3, X, ld_X, (cudaStream_t)stream, a0, w0);
 }
 
@@ -698,22 +781,26 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
         if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy of taps");
         taps_d = (const float*)c->stage[2];
     }
-    Io io;
-    if ((s = stage_in(c, x, batch, n, ld_x, st, &io)) != SPEC_OK) return s;
-    if ((s = stage_out_alloc(c, X, batch, K, ld_X, &io)) != SPEC_OK) return s;
+    if (!is_device_ptr(x) || !is_device_ptr(X))
+        return host_pipeline(c, x, batch, n, ld_x, X, K, ld_X, st,
+                             [&](const float* xd, int64_t ld_xd, float2* Xd, int64_t ld_Xd, int64_t nb) {
+                                 return spec_zoom(c, xd, nb, n, ld_xd, fs, f1, f2, d, taps_d, n_taps, n_fft,
+                                                  (float*)Xd, ld_Xd, stream);
+                             });
+    float2* X2 = reinterpret_cast<float2*>(X);
     cudaError_t e;
     if (p.big) {
         const float2* tab = nullptr;
         if ((s = plan_table(c, 1, p.fft, &tab)) != SPEC_OK) return s;
         if ((s = ensure_stage(c, 3, (size_t)batch * p.fft.LZ * sizeof(float2))) != SPEC_OK) return s;
-        e = zoom_big_launch(p, io.x, batch, ld_x, taps_d, (float2*)c->stage[3],
-                            c->block_tw + block_twiddle_offset(p.fft.LZ), tab, io.X, ld_X, st);
+        e = zoom_big_launch(p, x, batch, ld_x, taps_d, (float2*)c->stage[3],
+                            c->block_tw + block_twiddle_offset(p.fft.LZ), tab, X2, ld_X, st);
     } else {
-        e = zoom_launch(p, io.x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), io.X, ld_X, st,
+        e = zoom_launch(p, x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), X2, ld_X, st,
                         c->lanes == 2 ? 2 : 1);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
-    return stage_out_finish(c, X, batch, K, ld_X, st, io);
+    return SPEC_OK;
 }
 
 // ---- host helpers ----------------------------------------------------------
