@@ -264,8 +264,13 @@ __device__ __forceinline__ void epilogue(const FftArgs& a, float2 (&v)[E]) {
     float2* Xr = a.X + Xo;
     const float2* wp = a.tab + R * T + R * E;
     if (a.C == 1) {
-        for (int k = lt; k <= H / 2 && live; k += per_trace)
-            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], __ldg(wp + k));
+        // w_{2H}^k for k = lt + per_trace j as w^{lt} w^{per_trace j}: one
+        // coalesced table read per thread, then a broadcast one per pair
+        const float2 w0 = __ldg(wp + lt);
+        int kj = 0;
+#pragma unroll 4
+        for (int k = lt; k <= H / 2 && live; k += per_trace, kj += per_trace)
+            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], cmul(w0, __ldg(wp + kj)));
     } else {
         const int P = (H >> 1) / a.C;
         const int k0 = rank * P;
@@ -360,8 +365,13 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     float2* Xr = a.X + Xo;
     const float2* wp = a.tab + R * T + R * E;
     if (a.C == 1) {
-        for (int k = lt; k <= H / 2 && live; k += per_trace)
-            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], __ldg(wp + k));
+        // w_{2H}^k for k = lt + per_trace j as w^{lt} w^{per_trace j}: one
+        // coalesced table read per thread, then a broadcast one per pair
+        const float2 w0 = __ldg(wp + lt);
+        int kj = 0;
+#pragma unroll 4
+        for (int k = lt; k <= H / 2 && live; k += per_trace, kj += per_trace)
+            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], cmul(w0, __ldg(wp + kj)));
     } else {
         const int P = (H >> 1) / a.C;
         const int k0 = rank * P;
