@@ -142,6 +142,15 @@ template <bool INV> __device__ __forceinline__ void jpair(C2 t1, C2 d, C2& o1, C
     o3 = INV ? m : p;
 }
 
+// lane-wise complex products: C2 x C2, and one complex z times both lanes
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+    return C2{sub2(mul2(a.re, b.re), mul2(a.im, b.im)), fma2(a.re, b.im, mul2(a.im, b.re))};
+}
+__device__ __forceinline__ C2 cmul(float2 z, C2 b) {
+    const float2 zr = make_float2(z.x, z.x), zi = make_float2(z.y, z.y);
+    return C2{sub2(mul2(zr, b.re), mul2(zi, b.im)), fma2(zr, b.im, mul2(zi, b.re))};
+}
+
 // multiply by e^{-j pi/2} (forward) or e^{+j pi/2} (inverse)
 template <bool INV> __device__ __forceinline__ C2 rot90(C2 a) {
     return INV ? C2{vneg(a).im, a.re} : C2{a.im, vneg(a).re};

@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
 
     C2 v[E];
     {
-        const float2 wta = __ldg(a.tab + ra * T + t), wtb = __ldg(a.tab + rb * T + t);
+        // both lanes' pre-twiddles w_H^{r m} = w_H^{r t} w_H^{r T i} as one
+        // packed product, then the shared z[m] times both
+        const C2 wt = c2(__ldg(a.tab + ra * T + t), __ldg(a.tab + rb * T + t));
         const float2* wia = a.tab + R * T + ra * E;
         const float2* wib = a.tab + R * T + rb * E;
         const float* xr = a.x + xo;
@@ -331,8 +333,7 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
             float re = 0.f, im = 0.f;
             if (live && 2 * m < n) re = __ldg(xr + 2 * m);
             if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
-            const float2 z = make_float2(re, im);
-            v[i] = c2(cmul(z, cmul(wta, __ldg(wia + i))), cmul(z, cmul(wtb, __ldg(wib + i))));
+            v[i] = cmul(make_float2(re, im), cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
         }
     }
     FFT::run(v, s, t, a.tw);

@@ -413,8 +413,7 @@ bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, d
     // may run past L_out: those reads (results discarded) stay inside the
     // allocation, in the FFT area after the rows plus kZoomGroup T floats of
     // slack at the end.
-    int64_t rs = (lout - 1) + (n_taps - 1) / d + 2;
-    if ((rs & 1) == 0) ++rs;
+    const int64_t rs = zoom_rows(lout, n_taps, d);
     const size_t smem = (size_t)n_taps * 16 + (size_t)((d * rs + 1) / 2) * 8 +
                         (size_t)padded_len((int)K) * 8 + (size_t)kZoomGroup * T * 4;
     if (smem > 200 * 1024) {
@@ -456,9 +455,18 @@ cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_
 // ---------------------------------------------------------------------------
 // Ragged batches (per-trace parameters from RaggedItem).
 
+// Row stride of the polyphase layout: at least the columns a kept output
+// reads, (L_out - 1) + (L_h - 1)/D + 2.  A warp stages 32 consecutive samples,
+// D phases x 32/D columns; for D a power of two up to 32 the stride is m mod
+// 2m (m = 32/D), so the D rows start m banks apart and the warp's stores hit
+// 32 different banks.  Otherwise (and for D = 1) the stride is odd.
 int zoom_rows(int64_t lout, int64_t n_taps, int64_t d) {
-    int64_t rs = (lout - 1) + (n_taps - 1) / d + 2;
-    return (int)(rs | 1);
+    const int64_t need = (lout - 1) + (n_taps - 1) / d + 2;
+    if (d >= 2 && d <= 32 && is_pow2(d)) {
+        const int64_t m = 32 / d;
+        return (int)(need + ((m - need % (2 * m)) % (2 * m) + 2 * m) % (2 * m));
+    }
+    return (int)(need | 1);
 }
 
 size_t zoom_smem_for(int n_taps, int d, int rs, int K) {
