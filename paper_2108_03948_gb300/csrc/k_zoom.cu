@@ -39,27 +39,46 @@ constexpr int kZoomGroup = 4;   // outputs per thread per pass over the taps (at
 // FIR + decimate of one trace: thread t computes the G outputs
 // m = m0 + u T (u < G) per pass over the taps, each tap read once per G
 // multiply-add pairs, and stores u[m] e^{-j w m D} into s (padded index).
-template <int G, int T>
-__device__ __forceinline__ void zoom_fir(const float4* tap, const float* xs, float2* s, int n_taps, int lout,
-                                         uint64_t Cn, int D, int t) {
-    for (int m0 = t; m0 < lout; m0 += G * T) {
-        float re[G], im[G];
+// FIR + decimate (Eq. 8-10, polyphase): output m sums, over the phase rows
+// p, g[J - p - D c] xs[p rs + m + c] for c = 0 .. n_p - 1 (tap k = J - q,
+// q = p + D c), then takes the rotation of the mix.  A thread computes B
+// adjacent outputs, which read the same row window shifted by one sample: a
+// window of B samples slides along the row in registers, so each tap costs
+// one shared-memory read instead of B.  B = 3 keeps the threads' reads and
+// stores (stride B) on distinct banks.  A block that runs past L_out reads at
+// most up to index D rs (the FFT area, inside the allocation); its results
+// are discarded.
+template <int B, int T>
+__device__ __forceinline__ void zoom_fir_blocked(const float4* tap, const float* xs, float2* s, int n_taps,
+                                                 int lout, int rs, uint64_t Cn, int D, int t) {
+    const int J = n_taps - 1;
+    for (int m0 = B * t; m0 < lout; m0 += B * T) {
+        float re[B], im[B];
 #pragma unroll
-        for (int u = 0; u < G; ++u) re[u] = im[u] = 0.f;
-        const float* xm = xs + m0;
-        for (int k = 0; k < n_taps; ++k) {
-            const float4 g = tap[k];
-            const float* xk = xm + __float_as_int(g.z);
+        for (int u = 0; u < B; ++u) re[u] = im[u] = 0.f;
+        for (int p = 0; p < D && p <= J; ++p) {
+            const float* row = xs + p * rs + m0;
+            const float4* tp = tap + (J - p);                // tap of step c: tp[-D c]
+            const int np = (J - p) / D + 1;
+            float w[B];
 #pragma unroll
-            for (int u = 0; u < G; ++u) {
-                const float xv = xk[u * T];
-                re[u] = fmaf(g.x, xv, re[u]);
-                im[u] = fmaf(g.y, xv, im[u]);
+            for (int u = 0; u + 1 < B; ++u) w[u + 1] = row[u];
+#pragma unroll 3
+            for (int c = 0; c < np; ++c) {
+#pragma unroll
+                for (int u = 0; u + 1 < B; ++u) w[u] = w[u + 1];
+                w[B - 1] = row[c + B - 1];                   // window: w[u] = row[c + u]
+                const float4 g = tp[-D * c];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    re[u] = fmaf(g.x, w[u], re[u]);
+                    im[u] = fmaf(g.y, w[u], im[u]);
+                }
             }
         }
 #pragma unroll
-        for (int u = 0; u < G; ++u) {
-            const int m = m0 + u * T;
+        for (int u = 0; u < B; ++u) {
+            const int m = m0 + u;
             if (m < lout) {
                 const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
                 s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
@@ -127,14 +146,7 @@ __global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 1024 ? 1 : (
     }
     __syncthreads();
 
-    // FIR + decimate: groups of G outputs m = t + T (G g + u), G just large
-    // enough to cover L_out in one pass where possible (no idle slots)
-    switch (min(kZoomGroup, (lout + T - 1) / T)) {
-        case 1: zoom_fir<1, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
-        case 2: zoom_fir<2, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
-        case 3: zoom_fir<3, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
-        default: zoom_fir<4, T>(tap, xs, s, n_taps, lout, Cn, D, t); break;
-    }
+    zoom_fir_blocked<3, T>(tap, xs, s, n_taps, lout, rs, Cn, D, t);
     __syncthreads();
     float2 v[E];
 #pragma unroll
