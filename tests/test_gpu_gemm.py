@@ -104,6 +104,26 @@ def test_gemm_host_buffers_and_repeat(ctx, S):
     assert np.array_equal(np.asarray(h), d)
 
 
+def test_gemm_and_spiral_host_pipeline_chunks(ctx, S):
+    """Host buffers above 16 MiB run in overlapped chunks of traces; each row
+    of the product is computed by the same MMA sequence wherever its tile
+    lies, so the chunked host call equals the device-pointer call bit for
+    bit (4000 traces: chunks of 1024 and a ragged last one), on the unit
+    circle and off it."""
+    x = noise(4000, 1024, 9)
+    xd = dev(x)
+    d = S.spec_czt(ctx, xd, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    h = S.spec_czt(ctx, x, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3)
+    assert np.array_equal(np.asarray(h), d)
+    ds = S.spec_czt_spiral(ctx, xd, FS, 0.8e12, 1.2e12, 512, 1.0005, 0.9999).cpu().numpy()
+    hs = np.zeros((4000, 515), dtype=np.complex64)
+    S.spec_czt_spiral(ctx, x, FS, 0.8e12, 1.2e12, 512, 1.0005, 0.9999, out=hs[:, :512])
+    assert np.array_equal(hs[:, :512], ds)
+    assert not hs[:, 512:].any()
+    torch.cuda.synchronize()
+    assert S.ctx_status(ctx) == S.SPEC_OK
+
+
 def test_workload3_full_batch_sampled(ctx, S):
     cfg = synth.UNIFORM[3]
     idx = np.arange(cfg.batch)

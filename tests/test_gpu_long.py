@@ -140,6 +140,20 @@ def test_zoom_workload4_sampled(ctx, S):
 
 # ------------------------------------------------------ host buffers ------
 
+def test_long_paths_host_pipeline_chunks(ctx, S):
+    """Host buffers above 16 MiB of traffic run in chunks of traces: the
+    multi-pass FFT (20 traces to 2^18) and the segmented chirp-z (21 traces of
+    262144 samples, a 1024-bin band) give the device-pointer call's bits."""
+    x = noise(20, 200000, 12)
+    Xd = S.spec_fft(ctx, dev(x), FS, 1 << 18).cpu().numpy()
+    Xh = S.spec_fft(ctx, x, FS, 1 << 18)
+    assert np.array_equal(np.asarray(Xh), Xd)
+    y = noise(21, 262144, 13)
+    Zd = S.spec_czt(ctx, dev(y), FS, 0.3e12, 0.4e12, 1024).cpu().numpy()
+    Zh = S.spec_czt(ctx, y, FS, 0.3e12, 0.4e12, 1024)
+    assert np.array_equal(np.asarray(Zh), Zd)
+
+
 def test_long_paths_with_host_buffers(ctx, S):
     x = noise(2, 40000, 11)
     Xd = S.spec_fft(ctx, dev(x), FS, 65536).cpu().numpy()
