@@ -369,10 +369,32 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
         // w_{2H}^k for k = lt + per_trace j as w^{lt} w^{per_trace j}: one
         // coalesced table read per thread, then a broadcast one per pair
         const float2 w0 = __ldg(wp + lt);
-        int kj = 0;
+        if ((per_trace & 15) == 0) {
+            // Here H/2 = E per_trace, so k = lt + per_trace j (j < E) covers
+            // [0, H/2) and thread 0 adds k = H/2.  With per_trace a multiple
+            // of 16, pidx(k) and pidx(H - k) move by a constant step, so the
+            // fully unrolled loop addresses everything from three bases.
+            const int step = per_trace + (per_trace >> 4);
+            const float2* za = zs + pidx(lt);
+            const float2* zb = zs + pidx(H - lt);        // lt = 0: slot H/16 + H, not read at j = 0
+            if (live) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const float2 A = za[step * j];
+                    const float2 B = (j == 0 && lt == 0) ? A : zb[-step * j];
+                    unpack_pair(Xr, lt + per_trace * j, H, A, B, cmul(w0, __ldg(wp + per_trace * j)));
+                }
+                if (lt == 0) {
+                    const float2 Z = zs[pidx(H / 2)];
+                    unpack_pair(Xr, H / 2, H, Z, Z, __ldg(wp + H / 2));
+                }
+            }
+        } else {
+            int kj = 0;
 #pragma unroll 4
-        for (int k = lt; k <= H / 2 && live; k += per_trace, kj += per_trace)
-            unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], cmul(w0, __ldg(wp + kj)));
+            for (int k = lt; k <= H / 2 && live; k += per_trace, kj += per_trace)
+                unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], cmul(w0, __ldg(wp + kj)));
+        }
     } else {
         const int P = (H >> 1) / a.C;
         const int k0 = rank * P;
