@@ -327,13 +327,23 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
         const float2* wia = a.tab + R * T + ra * E;
         const float2* wib = a.tab + R * T + rb * E;
         const float* xr = a.x + xo;
+        if (live && n >= 2 * LZ) {
+            // the trace covers every packed slot: no per-sample bounds
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + T * i;
-            float re = 0.f, im = 0.f;
-            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
-            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
-            v[i] = cmul(make_float2(re, im), cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
+            for (int i = 0; i < E; ++i) {
+                const int m = t + T * i;
+                v[i] = cmul(make_float2(__ldg(xr + 2 * m), __ldg(xr + 2 * m + 1)),
+                            cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int m = t + T * i;
+                float re = 0.f, im = 0.f;
+                if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+                if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+                v[i] = cmul(make_float2(re, im), cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
+            }
         }
     }
     FFT::run(v, s, t, a.tw);
@@ -342,11 +352,24 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
     // this shared memory) before any of them writes Z into its peers.
     if (a.C > 1) cluster_arrive_relaxed_wait(); else __syncthreads();
     if (a.C == 1) {
+        const int TR = T << a.logR;
+        if ((TR & 15) == 0) {
+            // Z[R (t + T i) + r] sits at pidx(R t + r) + 17 (T R/16) i
+            const int st = (TR >> 4) * 17;
+            float2* pa = zs + pidx((t << a.logR) + ra);
+            float2* pb = zs + pidx((t << a.logR) + rb);
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int q = (t + T * i) << a.logR;
-            zs[pidx(q + ra)] = lane_a(v[i]);
-            zs[pidx(q + rb)] = lane_b(v[i]);
+            for (int i = 0; i < E; ++i) {
+                pa[st * i] = lane_a(v[i]);
+                pb[st * i] = lane_b(v[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int q = (t + T * i) << a.logR;
+                zs[pidx(q + ra)] = lane_a(v[i]);
+                zs[pidx(q + rb)] = lane_b(v[i]);
+            }
         }
         __syncthreads();
     } else {
