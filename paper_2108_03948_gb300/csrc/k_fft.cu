@@ -327,8 +327,15 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
         const float2* wia = a.tab + R * T + ra * E;
         const float2* wib = a.tab + R * T + rb * E;
         const float* xr = a.x + xo;
-        if (live && n >= 2 * LZ) {
-            // the trace covers every packed slot: no per-sample bounds
+        if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
+            // the trace covers every packed slot and the row is 8-byte
+            // aligned: each packed sample z[m] is one 8-byte load
+            const float2* x2 = reinterpret_cast<const float2*>(xr);
+#pragma unroll
+            for (int i = 0; i < E; ++i)
+                v[i] = cmul(__ldg(x2 + t + T * i), cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
+        } else if (live && n >= 2 * LZ) {
+            // full trace, odd row start: two 4-byte loads, no per-sample bounds
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int m = t + T * i;

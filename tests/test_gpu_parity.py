@@ -80,6 +80,21 @@ def test_fft_thz_traces_and_strides(ctx, S):
     assert torch.isnan(out[:, 8193:].real).all()        # padding columns untouched
 
 
+def test_fft_full_traces_at_odd_row_starts(ctx, S):
+    """Full traces (n = 2 LZ) load their packed samples as 8-byte pairs when
+    the row starts on an 8-byte boundary and as two 4-byte loads otherwise:
+    an odd row stride (2051) alternates the two cases row by row, and a base
+    offset by one float swaps them."""
+    x = traces(6, 2048, 77)
+    ref = O.fft_padded(x, 16384)
+    for off in (0, 1):
+        base = torch.zeros((6 * 2051 + 1,), dtype=torch.float32, device="cuda")
+        rows = base[off:off + 6 * 2051].view(6, 2051)
+        rows[:, :2048] = dev(x)
+        got = S.spec_fft(ctx, rows, 20e12, 16384, n=2048).cpu().numpy()
+        assert rel_rows(got, ref).max() <= TOL, off
+
+
 # ---------------------------------------------------------------- CZT ------
 
 CZT_CASES = [
