@@ -649,11 +649,12 @@ def run_ours(args):
             torch.distributed.barrier()
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(args.steps)]
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    if not os.path.isdir(out_dir):
+    if args.clocks_csv:
+        clocks_path = args.clocks_csv.replace("{rank}", str(rank))
+    else:
         import tempfile
-        out_dir = tempfile.gettempdir()
-    clocks = ClockSampler(local, os.path.join(out_dir, f"clocks_rank{rank}.csv"))
+        clocks_path = os.path.join(tempfile.gettempdir(), f"clocks_rank{rank}.csv")
+    clocks = ClockSampler(local, clocks_path)
     with clocks:
         barrier()
         torch.cuda.synchronize()
@@ -794,6 +795,9 @@ def main(argv=None):
     ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="where to write the clock samples of the timed region ({rank} is replaced); "
+                         "default: the temp directory")
     ap.add_argument("--batch", type=int, default=None,
                     help="traces per step for workloads 1, 3 and 4 (a smaller case for profiling; "
                          "the default is the workload's batch)")
