@@ -45,7 +45,7 @@ typedef enum {
     SPEC_EINVAL = 1,        /* bad argument (checked before any launch)        */
     SPEC_ENOMEM = 2,        /* device or host allocation failed                 */
     SPEC_ECUDA = 3,         /* a CUDA runtime call failed                       */
-    SPEC_EUNSUPPORTED = 4,  /* valid arguments beyond this build's size limits  */
+    SPEC_EUNSUPPORTED = 4,  /* valid arguments beyond the library's size limits */
     SPEC_ETIMEOUT = 5       /* a bounded device-side wait gave up               */
 } spec_status;
 

@@ -59,7 +59,7 @@ struct FftPlan {
     int threads = 0;
     size_t smem = 0;
 };
-// Returns false (with a reason) if the size needs a path this build lacks.
+// Returns false (with a reason) if the size needs a path the library lacks.
 bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why);
 // Per-plan twiddles (pre-twiddle factors and the unpack twiddle), float64 on
 // the host, rounded to float.
