@@ -123,8 +123,26 @@ __global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, F
     for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(&V[t + T * i]));
     int ti = t;                        // opaque copy: see k_czt_bluestein2
     asm volatile("" : "+r"(ti));
-    Iv::run(v, s, ti, a.tw);
     float2* Xr = a.X + Xo;
+    // A uniform batch (one M for every trace of the CTA) with M <= L/4 keeps
+    // only outputs t + T i with i < E/4: stored from a separate copy of the
+    // inverse FFT, whose unused last-pass outputs the compiler then drops.
+    // The choice depends on kernel arguments only, so every thread of the
+    // CTA takes the same branch (the FFT holds CTA barriers).
+    // (For L >= 4096 only: the second copy makes the smaller sizes spill
+    // at 64 registers.)
+    if constexpr (L >= 4096) {
+        if (!a.items && a.m <= L / 4) {
+            Iv::run(v, s, ti, a.tw);
+#pragma unroll
+            for (int i = 0; i < E / 4; ++i) {
+                const int k = t + T * i;
+                if (live && k < m) Xr[k] = cmul(v[i], __ldg(&post[k]));
+            }
+            return;
+        }
+    }
+    Iv::run(v, s, ti, a.tw);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int k = t + T * i;

@@ -207,6 +207,20 @@ def test_host_pipeline_chunks_match_device_path(ctx, S):
         assert np.array_equal(ow[:, :bins], ref), name                         # strided host rows
 
 
+def test_host_buffers_rejected_before_any_copy(ctx, S):
+    """A host-buffer call with a bad argument returns SPEC_EINVAL before the
+    pipeline starts: the caller's output buffer is untouched."""
+    lib = S.lib()
+    x = np.ones((3, 64), dtype=np.float32)
+    X = np.full((3, 64), 7 + 7j, dtype=np.complex64)
+    px, pX = x.ctypes.data, X.ctypes.data
+    E = S.SPEC_EINVAL
+    assert lib.spec_fft(ctx.handle, px, 3, 64, 64, 1.0, 1 << 25, pX, 64, None) == E          # n_fft
+    assert lib.spec_czt(ctx.handle, px, 3, 64, 64, 1.0, 0.0, 0.4, 8, 9, pX, 64, None) == E    # mode
+    assert lib.spec_zoom(ctx.handle, px, 3, 64, 64, 1.0, 0.1, 0.2, 3, px, 8, 64, pX, 64, None) == E  # d
+    assert (X == 7 + 7j).all()
+
+
 # --------------------------------------------------------------- errors ----
 
 def test_invalid_arguments_return_einval(ctx, S):
