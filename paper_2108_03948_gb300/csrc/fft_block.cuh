@@ -65,20 +65,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return mul2(a, make_float2(s, s)); }
 
 // multiply by e^{-j pi/2} (forward) or e^{+j pi/2} (inverse)
 template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-}
-
-// e^{-j 2 pi num/den} (forward) for an exact rational argument; sincospif
-// takes pi-multiples, so 2 num/den is passed (exact for den <= 2^24).
-template <bool INV> __device__ __forceinline__ float2 unit_rational(int num, int den) {
-    float s, c;
-    sincospif(2.0f * (float)num / (float)den, &s, &c);
-    return INV ? make_float2(c, s) : make_float2(c, -s);
 }
 
 // e^{sign j 2 pi ph/2^64}: `ph` is a phase in cycles as a 64-bit fixed-point
