@@ -49,6 +49,28 @@ def _time(f, reps: int, flush) -> float:
     return float(np.median(ts))
 
 
+def zoom_decimation(fs: float, f1: float, f2: float) -> int:
+    """The largest power of two D with fs / D >= 1.25 (f2 - f1): the decimated
+    rate still covers the band with a 25% guard."""
+    d = 1
+    while fs / (2 * d) >= 1.25 * (f2 - f1):
+        d *= 2
+    return d
+
+
+def sizes(fs: float, n: int, f1: float, f2: float, df: float, d: int, n_taps: int = 63):
+    """(N_FFT, M, K) of one resolution Delta f: N_FFT = ceil(fs / Delta f)
+    (Eq. 3, never below N), M = ceil((f2 - f1) N_FFT / fs) (Eq. 25), and the
+    Zoom FFT's K = N_FFT / D rounded up to a power of two and large enough for
+    the ceil((N + L_h - 1) / D) decimated samples."""
+    n_fft = max(n, math.ceil(fs / df))
+    m = spec.spec_m_for_resolution(fs, f1, f2, n_fft)
+    k = 1 << max(0, math.ceil(math.log2(n_fft / d)))
+    while (n + n_taps - 1 + d - 1) // d > k:
+        k *= 2
+    return n_fft, m, k
+
+
 def main(argv=None) -> int:
     import torch
     ap = argparse.ArgumentParser()
@@ -67,19 +89,13 @@ def main(argv=None) -> int:
     xd = torch.from_numpy(x).cuda()
     ctx = spec.Context(0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    D = 1
-    while fs / (2 * D) >= 1.25 * (f2 - f1):
-        D *= 2
+    D = zoom_decimation(fs, f1, f2)
     taps = torch.from_numpy(spec.spec_design_lowpass(63, D)).cuda()
     first = None
     print("delta_f_GHz n_fft fft_us czt_m czt_us zoom_D zoom_K zoom_us fft_rel czt_rel zoom_rel")
     for i in range(args.steps):
         df = 20e9 - 0.5e9 * i
-        n_fft = max(n, math.ceil(fs / df))
-        m = spec.spec_m_for_resolution(fs, f1, f2, n_fft)
-        K = 1 << max(0, math.ceil(math.log2(n_fft / D)))
-        while (n + 63 - 1 + D - 1) // D > K:
-            K *= 2
+        n_fft, m, K = sizes(fs, n, f1, f2, df, D)
         X = torch.empty((args.traces, n_fft // 2 + 1), dtype=torch.complex64, device="cuda")
         Z = torch.empty((args.traces, m), dtype=torch.complex64, device="cuda")
         U = torch.empty((args.traces, K), dtype=torch.complex64, device="cuda")
