@@ -1,26 +1,42 @@
-"""Benchmark: batched spectral estimation of THz-TDS traces on one GB300.
+"""Benchmark: batched spectral estimation of THz-TDS traces on GB300.
 
 A step is one pass of the whole hot path over one batch: the zero-padded FFT,
-the chirp-z transform (Bluestein) and the Zoom FFT of every trace, inputs
-resident in HBM.  The metric is spectral bins per second (FFT N_FFT/2+1,
-CZT M, Zoom N_FFT/D bins per trace).
+the chirp-z transform and the Zoom FFT of every trace, inputs resident in HBM.
+The metric is spectral bins per second (FFT N_FFT/2+1, CZT M, Zoom N_FFT/D
+bins per trace).
 
-Workloads (``--workload``):
-  1 (default) 4096 synthetic traces of N = 2048 float32 samples at fs = 20 THz
-    -- FFT to 16384, CZT 0.2-2.5 THz at M = 1024, Zoom FFT at 1.35 THz with
-    D = 4 and a 63-tap Hamming low-pass -- one launch per transform;
+Workloads (``--workload``, default ``all``):
+  3 (the headline: the largest single-GPU configuration) 65536 traces of
+    N = 1024 at fs = 20 THz -- FFT to 8192, chirp-z 0.8-1.2 THz at M = 512 as a
+    split-FP16 tensor-core product (the plain FP32 Bluestein form is timed on
+    the same batch beside it, giving the product's speed-up factor), Zoom FFT
+    at 1.0 THz with D = 4 and 63 taps;
+  1 4096 traces of N = 2048 -- FFT to 16384, CZT 0.2-2.5 THz at M = 1024,
+    Zoom FFT at 1.35 THz with D = 4 and a 63-tap Hamming low-pass;
   2 10000 ragged traces (N 1000-8192, per-trace band, M, D, taps;
-    N_FFT = 8 nextpow2(N)) -- one CUDA-graph launch per transform.
+    N_FFT = 8 nextpow2(N)) -- one CUDA-graph launch per transform;
+  4 256 traces of N = 262144 -- FFT to 2^21, CZT 0.3-0.4 THz at M = 65536,
+    Zoom FFT D = 64 with 255 taps.
+With ``all`` the JSON line's ``value``/``config``/``roofline`` are workload 3's
+and ``workloads`` holds every workload's own figures.
 
-Timing: W warm-up steps, then K steps; before each step a 256 MB buffer is
-written to flush L2 (outside the per-step events).  Every transform is
-bracketed by CUDA events on the stream it runs on; the step time is the sum.
-Multi-process (torchrun): each rank runs the same per-GPU batch (weak
-scaling, no collective on the data path); the reported time is the max over
-ranks and `value` counts the bins of all ranks.
+Timing: W warm-up steps, then K timed steps per workload (workloads other
+than the headline cap K to keep the run within minutes); before each step a
+256 MB buffer is written to flush L2 (outside the per-step events).  Every
+transform is bracketed by CUDA events on the stream it runs on; the step time
+is the sum.
+
+Multi-GPU: ``--gpus N`` without a torchrun environment starts N ranks itself
+(torch.distributed.run on 127.0.0.1).  The ranks partition one global batch of
+N times the per-GPU workload (weak scaling; ``--scaling strong`` keeps the
+global batch at one workload and splits it): contiguous trace slices for the
+uniform workloads, a cost-balanced split of the descriptor list for the
+ragged one (``paper_2108_03948_gb300.shard``).  No collective is on the data
+path; the reported time is the max over ranks and ``value`` counts every
+rank's bins.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm of
-this comparison): each step is a bounded sample of the same workload.
+this comparison): each step is a bounded sample of the headline workload.
 """
 from __future__ import annotations
 
@@ -71,9 +87,21 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def job_throughput(bins_per_rank_step: int, steps: int, world: int, max_seconds: float) -> float:
-    """Whole-job bins/s: every rank processes its own batch (weak scaling)."""
-    return world * bins_per_rank_step * steps / max_seconds
+def job_throughput(bins_all_ranks_step: int, steps: int, max_seconds: float) -> float:
+    """Whole-job bins/s: the bins of every rank's share of the global batch per
+    step, over the slowest rank's elapsed time."""
+    return bins_all_ranks_step * steps / max_seconds
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    """Sum of a per-rank count (bins of the rank's share) across the group."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -311,9 +339,10 @@ def cpu_threads():
 # FP64 oracle.
 
 def oracle_uniform(cfg, n_traces):
-    """Time the oracle on the first n_traces of workload 1: (bins, s, outputs)."""
+    """Time the oracle on the first n_traces of a uniform workload: (bins, s,
+    outputs)."""
     from oracle import spec_oracle as O
-    x = synth.batch_traces(1, range(n_traces))
+    x = synth.batch_traces(cfg.workload, range(n_traces))
     taps = O.design_lowpass(cfg.zoom_taps, cfg.zoom_d)
     t0 = time.perf_counter()
     outs = {
@@ -375,12 +404,15 @@ def oracle_ragged(items, traces, pick, max_bins=None):
 
 
 def run_reference(args):
+    """The oracle arm: bounded samples of the headline workload (3, or the
+    one ``--workload`` names), timed on the host cores."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     times, bins_tot = [], 0
     steps = max(1, args.steps)
-    if args.workload == 2:
+    wl = 3 if args.workload == "all" else int(args.workload)
+    if wl == 2:
         # Per step one ragged trace, a different one each step (stride 9973
         # through the 10000) so that the sample spans the mix of sizes, and
         # per transform an evenly strided subset of its bins; the subset
@@ -397,18 +429,33 @@ def run_reference(args):
             bins_tot += b
         sample, name = f"1 of 10000 ragged traces per step (a new one each step), at most {nb} evenly strided " \
                        "bins of each of the three transforms", W2_NAME
+    elif wl == 4:
+        cfg = synth.UNIFORM[4]
+        x = synth.batch_traces(4, range(1))
+        from oracle import spec_oracle as O
+        taps = O.design_lowpass(cfg.zoom_taps, cfg.zoom_d)
+        nb = max(16, min(1024, 4096 // steps))
+        for _ in range(max(0, args.warmup)):
+            oracle_uniform_sample(cfg, x, [0], taps, 8)
+        for _ in range(steps):
+            b, dt, _, _ = oracle_uniform_sample(cfg, x, [0], taps, nb)
+            times.append(dt)
+            bins_tot += b
+        sample, name = f"1 trace per step, at most {nb} evenly strided bins of each transform", W4_NAME
     else:
         # Traces per step shrink as K grows so that the run stays near a
-        # fixed CPU budget (about 40k traces in total).
-        cfg = synth.UNIFORM[1]
-        per = max(8, min(1024, 40960 // steps))
+        # fixed CPU budget.
+        cfg = synth.UNIFORM[wl]
+        budget = 40960 if wl == 1 else 30720
+        per = max(8, min(1024, budget // steps))
         for _ in range(max(0, args.warmup)):
             oracle_uniform(cfg, 8)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b, dt, _ = oracle_uniform(cfg, per)
             times.append(dt)
             bins_tot += b
-        sample, name = f"{per} of 4096 traces per step, all bins of all three transforms", W1_NAME
+        sample, name = f"{per} of {cfg.batch} traces per step, all bins of all three transforms", \
+            {1: W1_NAME, 3: W3_NAME}[wl]
     value = bins_tot / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "bins/s", "n_gpus": args.gpus,
@@ -425,23 +472,40 @@ def run_reference(args):
 
 # --------------------------------------------------------------- workloads --
 
+def rank_share(workload, rank, world, scaling):
+    """This rank's global trace indices of a uniform workload, and the
+    global batch: weak scaling gives each rank a whole workload's batch of its
+    own traces, strong scaling splits one workload's batch."""
+    from paper_2108_03948_gb300 import shard
+    per = synth.UNIFORM[workload].batch
+    total = per * world if scaling == "weak" else per
+    a, b = shard.contiguous_slices(total, world)[rank]
+    return list(range(a, b)), total
+
+
 class Uniform:
     """Workloads 1, 3 and 4: a batch of equal traces, one launch sequence per
     transform (1: 4096 x 2048 samples; 3: 65536 x 1024, chirp-z on the
-    tensor cores; 4: 256 x 262144, multi-pass FFT and chirp-z)."""
+    tensor cores; 4: 256 x 262144, multi-pass FFT and chirp-z).  ``indices``
+    are the global trace indices this rank transforms."""
 
-    def __init__(self, spec, ctx, dev, workload=1, batch=None):
+    def __init__(self, spec, ctx, dev, workload=1, batch=None, indices=None):
         import torch
         self.workload = workload
         cfg = self.cfg = synth.UNIFORM[workload]
-        B = self.B = cfg.batch if batch is None else int(batch)
+        if indices is None:
+            indices = list(range(cfg.batch if batch is None else int(batch)))
+        elif batch is not None:
+            indices = list(indices)[:int(batch)]
+        self.indices = list(indices)
+        B = self.B = len(self.indices)
         self.spec, self.ctx = spec, ctx
         if workload == 3:
             # copies of 1024 distinct traces keep the host-side generation short
-            base = synth.batch_traces(3, range(min(B, 1024)))
+            base = synth.batch_traces(3, self.indices[:1024])
             self.x = np.ascontiguousarray(np.resize(base, (B, cfg.n)))
         else:
-            self.x = synth.batch_traces(workload, range(B))
+            self.x = synth.batch_traces(workload, self.indices)
         self.xd = torch.from_numpy(self.x).to(dev)
         self.taps_h = spec.spec_design_lowpass(cfg.zoom_taps, cfg.zoom_d)
         self.taps_d = torch.from_numpy(self.taps_h).to(dev)
@@ -449,6 +513,7 @@ class Uniform:
         c = {"fft": trace_cost("fft", cfg.n, cfg.n_fft),
              "czt": trace_cost("czt_gemm" if workload == 3 else "czt", cfg.n, m=cfg.czt_m),
              "zoom": trace_cost("zoom", cfg.n, cfg.zoom_n_fft, d=cfg.zoom_d, taps=cfg.zoom_taps)}
+        self.cost = c
         self.bins = {k: B * v[0] for k, v in c.items()}
         self.bytes = {k: B * v[1] for k, v in c.items()}
         self.flops = {k: B * v[2] for k, v in c.items()}
@@ -498,40 +563,50 @@ class Uniform:
         d2h = sum(v.numel() * 8 for v in self.out.values())
         return step, check, h2d, d2h
 
-    def cpu_leg(self):
+    def sample_pick(self):
         if self.workload == 1:
-            b, dt, ref = oracle_uniform(self.cfg, self.B)
-            errs = {}
-            for k, got in self.out.items():
-                g = got.cpu().numpy().astype(np.complex128)
-                errs[k] = float((np.linalg.norm(g - ref[k], axis=1) / np.linalg.norm(ref[k], axis=1)).max())
-            cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
-                   "sample": f"the whole batch ({self.B} traces), all bins of FFT, CZT and Zoom FFT, FP64 numpy, "
-                             f"{dt:.1f} s"}
-            return cpu, errs, "max_rel_l2_all_traces"
-        # workloads 3 and 4: a bounded sample (traces; bins for the long traces)
-        pick = list(range(min(4, self.B))) if self.workload == 4 else list(range(0, min(self.B, 1024), 16))
-        max_bins = 512 if self.workload == 4 else None
+            return list(range(self.B)), None
+        if self.workload == 4:
+            return list(range(min(4, self.B))), 512
+        return list(range(0, min(self.B, 1024), 16)), None
+
+    def cpu_leg(self):
+        """The oracle on a bounded sample of this rank's traces: its timing and
+        the worst relative L2 of the timed GPU outputs against it."""
+        pick, max_bins = self.sample_pick()
         b, dt, ref, kb = oracle_uniform_sample(self.cfg, self.x, pick, self.taps_h, max_bins)
         errs = {}
         for k, got in self.out.items():
             g = got[pick].cpu().numpy().astype(np.complex128)[:, kb[k]]
             errs[k] = float((np.linalg.norm(g - ref[k], axis=1) / np.linalg.norm(ref[k], axis=1)).max())
+        self.oracle_ref = (pick, kb, ref)
         what = "all bins" if max_bins is None else f"at most {max_bins} evenly strided bins of each transform"
+        whole = "the whole batch" if len(pick) == self.B else f"{len(pick)} of {self.B} traces"
         cpu = {"value": b / dt, "unit": "bins/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{len(pick)} of {self.B} traces, {what}, FP64 numpy, {dt:.1f} s"}
-        return cpu, errs, "max_rel_l2_sampled"
+               "sample": f"{whole}, {what}, FP64 numpy, {dt:.1f} s"}
+        return cpu, errs, ("max_rel_l2_all_traces" if len(pick) == self.B and max_bins is None
+                           else "max_rel_l2_sampled")
+
+    def rel_l2_vs_oracle(self, got):
+        """Worst relative L2 of a chirp-z output against the oracle sample."""
+        pick, kb, ref = self.oracle_ref
+        g = got[pick].cpu().numpy().astype(np.complex128)[:, kb["czt"]]
+        return float((np.linalg.norm(g - ref["czt"], axis=1) / np.linalg.norm(ref["czt"], axis=1)).max())
 
 
 class Ragged:
-    """Workload 2: 10000 ragged traces, one graph launch per transform."""
+    """Workload 2: ragged traces, one graph launch per transform.  ``indices``
+    are the global trace indices (of a list of ``total``) this rank
+    transforms."""
 
-    def __init__(self, spec, ctx, dev, count=10000):
+    def __init__(self, spec, ctx, dev, count=10000, indices=None, total=None):
         import torch
         self.spec, self.ctx = spec, ctx
-        rg = synth.ragged_params(count)
-        self.items = rg.items
-        self.traces = [synth.ragged_trace(i, it) for i, it in enumerate(self.items)]
+        total = count if total is None else total
+        rg = synth.ragged_params(total)
+        self.indices = list(range(count)) if indices is None else list(indices)
+        self.items = [rg.items[i] for i in self.indices]
+        self.traces = [synth.ragged_trace(g, it) for g, it in zip(self.indices, self.items)]
         xo = np.concatenate([[0], np.cumsum([len(t) for t in self.traces])[:-1]]).astype(np.int64)
         self.x = np.concatenate(self.traces)
         self.xd = torch.from_numpy(self.x).to(dev)
@@ -554,8 +629,9 @@ class Ragged:
             self.descs[name] = (kind, [spec.spec_desc(int(xo[i]), it.n, int(oo[i]), it.f1, it.f2, it.n_fft, it.m,
                                                       it.d, int(to[i]), it.n_taps) for i, it in enumerate(self.items)])
             self.out[name] = torch.empty(int(nb.sum()), dtype=torch.complex64, device=dev)
-        self.bound = {}
-        self.name = W2_NAME
+        self.bound = {"fft": "hbm", "czt": "alu", "zoom": None}
+        self.name = W2_NAME if len(self.items) == 10000 else \
+            f"{len(self.items)} of {total} ragged traces (cost-balanced share): " + W2_NAME
 
     def parts(self):
         s, ctx = self.spec, self.ctx
@@ -617,92 +693,31 @@ class Ragged:
 
 # ---------------------------------------------------------------- our arm --
 
-def run_ours(args):
+def timed_parts(parts, steps, warmup, flush, stream):
+    """W warm-ups, then per step: flush L2, CUDA events around every part on
+    its stream.  Returns {name: [ms per step]}."""
     import torch
-    from paper_2108_03948_gb300 import spec
-
-    rank, world, local = env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    ctx = spec.Context(local)
-    W = Ragged(spec, ctx, dev) if args.workload == 2 else Uniform(spec, ctx, dev, args.workload, args.batch)
-    fp32_peak, fp32_src = FP32_PEAK_TFLOPS, "nominal 152 SM x 128 lanes x 2 x 2.07 GHz"
-    try:
-        meas = spec.spec_measure_fp32_peak(ctx)
-        if meas > 0:
-            fp32_peak, fp32_src = meas, "measured (packed FP32 FMA microbenchmark, this run)"
-    except Exception:
-        pass
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    parts = W.parts()
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         for _, f in parts:
             f()
     torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(args.steps)]
-    if args.clocks_csv:
-        clocks_path = args.clocks_csv.replace("{rank}", str(rank))
-    else:
-        import tempfile
-        clocks_path = os.path.join(tempfile.gettempdir(), f"clocks_rank{rank}.csv")
-    clocks = ClockSampler(local, clocks_path)
-    with clocks:
-        barrier()
-        torch.cuda.synchronize()
-        for s in range(args.steps):
-            flush.zero_()
-            evs[s][0].record(stream)
-            for i, (_, f) in enumerate(parts):
-                f()
-                evs[s][i + 1].record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    per = {name: [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)]
-           for i, (name, _) in enumerate(parts)}
-    step_ms = [sum(per[name][s] for name, _ in parts) for s in range(args.steps)]
-    total_ms = max_over_ranks(sum(step_ms), world, dev)
-    bins_step = sum(W.bins.values())
-    value = job_throughput(bins_step, args.steps, world, total_ms / 1e3)
-    launches = W.launches() * args.steps
-
-    e2e_step, e2e_check, h2d, d2h = W.e2e()
-    e2e_step()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(steps)]
+    for s in range(steps):
+        flush.zero_()
+        evs[s][0].record(stream)
+        for i, (_, f) in enumerate(parts):
+            f()
+            evs[s][i + 1].record(stream)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 10))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e_val = job_throughput(bins_step, e2e_steps, world, e2e_s)
-    e2e_diff = e2e_check()
-    link = host_link_gbs(dev)
-    # copy-bound step time: each direction at its own measured rate, the two
-    # overlapping (bounded below by the duplex rate on the sum)
-    copy_ms = 1e3 * max(h2d / (link["h2d_gbs"] * 1e9), d2h / (link["d2h_gbs"] * 1e9),
-                        (h2d + d2h) / (link["duplex_gbs"] * 1e9))
-    e2e_ms = 1e3 * e2e_s / e2e_steps
+    return {name: [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(steps)]
+            for i, (name, _) in enumerate(parts)}
 
-    if rank != 0:
-        ctx.close()
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return 0
 
-    hbm, hbm_kind = measured_peaks()
-    tensor_peak, tensor_src = measured_tensor_peak()
+def kernel_figures(W, per, hbm, tensor_peak, fp32_peak):
+    """Per transform: median time, bins/s and the fraction of each roofline;
+    the binding roof is the one with the longer attainable time."""
     kern = {}
-    for name, _ in parts:
+    for name in per:
         ms = statistics.median(per[name])
         sec = ms / 1e3
         gbs = W.bytes[name] / sec / 1e9
@@ -715,10 +730,14 @@ def run_ours(args):
         else:
             k.update(fp32_tflops=tfl, fp32_frac=tfl / fp32_peak)
             t_cmp, cmp_name = W.flops[name] / (fp32_peak * 1e12), "alu"
-        # the binding roof is the one with the longer attainable time
         k["bound"] = "hbm" if t_hbm >= t_cmp else cmp_name
         k["frac"] = max(t_hbm, t_cmp) / sec
         kern[name] = k
+    return kern
+
+
+def roofline_of(kern, workload, peaks):
+    hbm, hbm_kind, tensor_peak, tensor_src, fp32_peak, fp32_src = peaks
     dom = max(kern, key=lambda k: kern[k]["ms"])
     kd = kern[dom]
     if kd["bound"] == "hbm":
@@ -731,55 +750,214 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": kd["fp32_tflops"], "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": kd["fp32_frac"], "peak_source": fp32_src}
     roof["kernel"] = dom
-    roof["traffic"] = traffic_for(args.workload, dom)
+    roof["traffic"] = traffic_for(workload, dom)
+    return roof
+
+
+def measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, scaling):
+    """Time one workload on this rank's share: device-timed steps, the
+    end-to-end leg, the oracle sample (rank 0, one GPU) and, for workload 3,
+    the FP32 Bluestein form of the chirp-z on the same batch."""
+    import torch
+    spec, ctx, dev, flush, stream, rank, world = ctx_tuple
+    if wl == 2:
+        from paper_2108_03948_gb300 import shard
+        per = 10000
+        total = per * world if scaling == "weak" else per
+        rg = synth.ragged_params(total)
+        costs = [shard.ragged_trace_cost(it.n, it.n_fft, it.m, it.d, it.n_taps) for it in rg.items]
+        parts_idx = shard.balance_by_cost(costs, world)
+        W = Ragged(spec, ctx, dev, count=len(parts_idx[rank]), indices=parts_idx[rank], total=total)
+        share = {"traces": len(parts_idx[rank]), "of": total, "split": "cost-balanced (greedy LPT)",
+                 "imbalance": shard.imbalance(costs, parts_idx)}
+    else:
+        idx, total = rank_share(wl, rank, world, scaling)
+        W = Uniform(spec, ctx, dev, wl, args.batch, indices=idx)
+        share = {"traces": W.B, "of": total, "split": "contiguous slice"}
+    parts = W.parts()
+    per = timed_parts(parts, steps, args.warmup, flush, stream)
+    step_ms = [sum(per[name][s] for name, _ in parts) for s in range(steps)]
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    bins_step = sum(W.bins.values())
+    bins_all = sum_over_ranks(bins_step, world, dev)
+    value = job_throughput(bins_all, steps, total_ms / 1e3)
+    launches = W.launches()
+
+    e2e_step, e2e_check, h2d, d2h = W.e2e()
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(steps, 10))
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_val = job_throughput(bins_all, e2e_steps, e2e_s)
+    e2e_diff = e2e_check()
+    e2e_ms = 1e3 * e2e_s / e2e_steps
+
+    hbm, _, tensor_peak, _, fp32_peak, _ = peaks
+    kern = kernel_figures(W, per, hbm, tensor_peak, fp32_peak)
+    res = {"workload": W.name, "value": value, "unit": "bins/s", "steps": steps,
+           "ms_per_step": statistics.mean(step_ms), "bins_per_step_per_gpu": bins_step, "share": share,
+           "kernels": kern, "roofline": roofline_of(kern, wl, peaks), "gpu_launches_per_step": launches,
+           "e2e": {"value": e2e_val, "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "steps": e2e_steps, "ms_per_step": e2e_ms, "max_abs_diff_vs_device_path": e2e_diff}}
+    cpu = None
+    if want_cpu:
+        cpu, errs, key = W.cpu_leg()
+        for k, v in errs.items():
+            kern[k][key] = v
+        res["cpu_baseline"] = cpu
+    if wl == 3:
+        # The plain per-trace FP32 form of the chirp-z on the same batch:
+        # the tensor-core product's speed-up at the same accuracy.
+        cfg = W.cfg
+        xb = torch.empty_like(W.out["czt"])
+        bl = [("czt_bluestein", lambda: spec.spec_czt(ctx, W.xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m,
+                                                       mode=spec.SPEC_CZT_BLUESTEIN, out=xb))]
+        pb = timed_parts(bl, max(5, min(steps, 50)), args.warmup, flush, stream)
+        b_ms = statistics.median(pb["czt_bluestein"])
+        g_ms = kern["czt"]["ms"]
+        cmp = {"gemm_mode": "SPEC_CZT_GEMM_F16X3", "gemm_ms": g_ms, "bluestein_fp32_ms": b_ms,
+               "factor": b_ms / g_ms, "what": "same 65536-trace batch, L2 flushed, CUDA events"}
+        if want_cpu:
+            cmp["gemm_rel_l2"] = kern["czt"].get("max_rel_l2_sampled")
+            cmp["bluestein_rel_l2"] = W.rel_l2_vs_oracle(xb)
+        res["czt_gemm_vs_bluestein"] = cmp
+        del xb
+    res["_W"] = W
+    return res
+
+
+def relaunch_under_torchrun(args, argv):
+    """--gpus N (N > 1) outside a torchrun environment: start N local ranks
+    with torch.distributed.run on 127.0.0.1 and return its exit status."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
+def run_ours(args):
+    import torch
+    from paper_2108_03948_gb300 import spec
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = spec.Context(local)
+    fp32_peak, fp32_src = FP32_PEAK_TFLOPS, "nominal 152 SM x 128 lanes x 2 x 2.07 GHz"
+    try:
+        meas = spec.spec_measure_fp32_peak(ctx)
+        if meas > 0:
+            fp32_peak, fp32_src = meas, "measured (packed FP32 FMA microbenchmark, this run)"
+    except Exception:
+        pass
+    hbm, hbm_kind = measured_peaks()
+    tensor_peak, tensor_src = measured_tensor_peak()
+    peaks = (hbm, hbm_kind, tensor_peak, tensor_src, fp32_peak, fp32_src)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx_tuple = (spec, ctx, dev, flush, stream, rank, world)
+
+    if args.workload == "all":
+        order, head = [3, 1, 2, 4], 3
+    else:
+        order, head = [int(args.workload)], int(args.workload)
+    caps = {1: 200, 2: 40, 3: 1 << 30, 4: 30}
+    want_cpu = world == 1 and not args.no_cpu_baseline and rank == 0
+    if args.clocks_csv:
+        clocks_path = args.clocks_csv.replace("{rank}", str(rank))
+    else:
+        import tempfile
+        clocks_path = os.path.join(tempfile.gettempdir(), f"clocks_rank{rank}.csv")
+    clocks = ClockSampler(local, clocks_path)
+    results = {}
+    t_start = time.perf_counter()
+    with clocks:
+        for wl in order:
+            steps = args.steps if wl == head else max(1, min(args.steps, caps[wl]))
+            r = measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, args.scaling)
+            W = r.pop("_W")
+            if wl == head:
+                head_W = W
+            else:
+                del W
+                torch.cuda.empty_cache()
+            results[wl] = r
+    wall = time.perf_counter() - t_start
+    link = host_link_gbs(dev)
+
+    if rank != 0:
+        ctx.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    h = results[head]
+    e2e = dict(h["e2e"])
+    copy_ms = 1e3 * max(e2e["h2d_bytes_per_step"] / (link["h2d_gbs"] * 1e9),
+                        e2e["d2h_bytes_per_step"] / (link["d2h_gbs"] * 1e9),
+                        (e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]) / (link["duplex_gbs"] * 1e9))
+    e2e.update(link={k: round(v, 1) for k, v in link.items()}, copy_bound_ms=copy_ms,
+               frac_of_copy_bound=copy_ms / e2e["ms_per_step"])
 
     # cuFFT beside our FFT (a reported comparison, not the target):
     # torch.fft.rfft(x, n=N_FFT), which pads internally, same timing protocol
     lib_cmp = None
-    if hasattr(W, "cfg") and world == 1:
+    if hasattr(head_W, "cfg") and world == 1:
         try:
-            n_fft = W.cfg.n_fft
+            n_fft = head_W.cfg.n_fft
             ts = []
             for it in range(8):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                torch.fft.rfft(W.xd, n=n_fft)
+                torch.fft.rfft(head_W.xd, n=n_fft)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 if it >= 3:
                     ts.append(e0.elapsed_time(e1))
-            lib_cmp = {"cufft_rfft_ms": statistics.median(ts), "ours_fft_ms": kern["fft"]["ms"],
+            lib_cmp = {"cufft_rfft_ms": statistics.median(ts), "ours_fft_ms": h["kernels"]["fft"]["ms"],
                        "what": "torch.fft.rfft(x, n=N_FFT) on the same device batch (cuFFT; pads internally)"}
         except Exception as ex:              # a comparison only; never fails the bench
             lib_cmp = {"unavailable": str(ex)[:120]}
 
-    # CPU-baseline leg (rank 0, N = 1 only): the FP64 oracle, timed; its
-    # outputs also give the parity of the timed GPU outputs.
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu, errs, key = W.cpu_leg()
-        for k, v in errs.items():
-            kern[k][key] = v
-
+    others = {}
+    for wl, r in results.items():
+        if wl == head:
+            continue
+        o = {k: v for k, v in r.items() if k not in ("bins_per_step_per_gpu",)}
+        others[str(wl)] = o
     line = {
-        "metric": METRIC, "value": value, "unit": "bins/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(step_ms),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "metric": METRIC, "value": h["value"], "unit": "bins/s", "n_gpus": world, "steps": h["steps"],
+        "warmup": max(3, args.warmup), "ms_per_step": h["ms_per_step"],
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": W.name, "l2": "flushed before every step (256 MB write)",
-                   "bins_per_step_per_gpu": bins_step},
-        "roofline": roof,
-        "kernels": kern,
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps, "max_abs_diff_vs_device_path": e2e_diff, "ms_per_step": e2e_ms,
-                "link": {k: round(v, 1) for k, v in link.items()}, "copy_bound_ms": copy_ms,
-                "frac_of_copy_bound": copy_ms / e2e_ms},
-        "gpu_launches": launches,
+        "config": {"workload": h["workload"], "l2": "flushed before every step (256 MB write)",
+                   "bins_per_step_per_gpu": h["bins_per_step_per_gpu"], "share": h["share"],
+                   "parallelism": f"trace-sharded over {world} GPU(s), no data-path collective"},
+        "roofline": h["roofline"],
+        "kernels": h["kernels"],
+        "cpu_baseline": h.get("cpu_baseline"),
+        "e2e": e2e,
+        "gpu_launches": h["gpu_launches_per_step"] * h["steps"],
         "clocks": clocks.summary(),
         "library_comparison": lib_cmp,
+        "workloads": others,
+        "wall_s": wall,
     }
+    if "czt_gemm_vs_bluestein" in h:
+        line["czt_gemm_vs_bluestein"] = h["czt_gemm_vs_bluestein"]
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -788,12 +966,16 @@ def run_ours(args):
 
 
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else list(argv)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4])
+    ap.add_argument("--workload", default="all", choices=["all", "1", "2", "3", "4"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: each rank transforms a whole workload of its own traces; strong: the ranks "
+                         "split one workload's batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="where to write the clock samples of the timed region ({rank} is replaced); "
@@ -802,6 +984,8 @@ def main(argv=None):
                     help="traces per step for workloads 1, 3 and 4 (a smaller case for profiling; "
                          "the default is the workload's batch)")
     args = ap.parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return relaunch_under_torchrun(args, argv)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -213,7 +213,10 @@ SPEC_API spec_status spec_zoom(spec_ctx* ctx, const float* x, int64_t batch, int
  *     make that first call before any stream capture;
  *   - every call rewrites the chirp tables in that shared array, so calls
  *     that overlap on the GPU (e.g. on two streams) race: order them on one
- *     stream.
+ *     stream;
+ *   - the set-up belongs to the device's CUDA context: do not use this entry
+ *     point across a cudaDeviceReset in the same process (the array is
+ *     reloaded and its twiddles are lost while the set-up is remembered).
  * Returns SPEC_ECUDA if a CUDA call fails.
  */
 SPEC_API spec_status spec_czt_static(const float* x, int64_t batch, int64_t n, int64_t ld_x,

@@ -17,6 +17,11 @@
 // twiddle part of the array and synchronises the caller's stream; make that
 // first call before any stream capture.
 //
+// The cached address and the twiddles belong to the device's current CUDA
+// context: after cudaDeviceReset the array is reloaded (zeroed, possibly at
+// another address) while the cache still says "set up", so this entry point
+// must not be used across a cudaDeviceReset in the same process.
+//
 // Every call shares the array and leaves its tables there.  Nothing in it
 // has to start at zero: each call rewrites the chirp tables and the kernel
 // spectrum it reads.  Two calls that run at the same time on the GPU (say on
@@ -111,7 +116,8 @@ extern "C" spec_status spec_czt_static(const float* x, int64_t batch, int64_t n,
                                        void* stream) {
     if (!x || !X || batch < 0 || n < 1 || m < 1 || ld_x < n || ld_X < m) return SPEC_EINVAL;
     if (!(fs > 0.0) || !std::isfinite(fs) || !std::isfinite(f1) || !std::isfinite(f2)) return SPEC_EINVAL;
-    if (n + m - 1 > kStaticMaxL) return SPEC_EUNSUPPORTED;
+    // n and m are bounded first, so that n + m - 1 cannot overflow
+    if (n > kStaticMaxL || m > kStaticMaxL || n + m - 1 > kStaticMaxL) return SPEC_EUNSUPPORTED;
     if (batch == 0) return SPEC_OK;
     const uintptr_t px = (uintptr_t)x, pX = (uintptr_t)X;
     const uintptr_t bx = (uintptr_t)(((batch - 1) * ld_x + n) * sizeof(float));
