@@ -24,6 +24,7 @@ struct CztEntry {
 struct FftEntry {
     int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables, 2: multi-pass twiddles (H = period log2)
     int H = 0, LZ = 0, emax = 16;
+    bool fixed = false;  // kind 0 with the packed tables of the fixed two-lane kernel
     float2* tab = nullptr;
 };
 

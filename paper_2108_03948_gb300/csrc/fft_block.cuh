@@ -166,11 +166,17 @@ template <> struct TwEntry<C2> { using type = float2; };
 template <bool INV> __device__ __forceinline__ float2 mul_tw(float2 a, float2 w) {
     return INV ? cmulc(a, w) : cmul(a, w);
 }
-template <bool INV> __device__ __forceinline__ C2 mul_tw(C2 a, float2 w) {
-    const float2 cc = make_float2(w.x, w.x), ss = make_float2(w.y, w.y);
+template <bool INV> __device__ __forceinline__ C2 mul_tw_pairs(C2 a, float2 cc, float2 ss) {
     const float2 rc = mul2(a.re, cc), ic = mul2(a.im, cc);
     if (INV) return C2{fma2(a.im, ss, rc), sub2(ic, mul2(a.re, ss))};
     return C2{sub2(rc, mul2(a.im, ss)), fma2(a.re, ss, ic)};
+}
+template <bool INV> __device__ __forceinline__ C2 mul_tw(C2 a, float2 w) {
+    return mul_tw_pairs<INV>(a, make_float2(w.x, w.x), make_float2(w.y, w.y));
+}
+// Twiddle stored as the packed pairs (c, c, s, s): no register shuffles.
+template <bool INV> __device__ __forceinline__ C2 mul_tw(C2 a, float4 w) {
+    return mul_tw_pairs<INV>(a, make_float2(w.x, w.y), make_float2(w.z, w.w));
 }
 
 // shared-memory element of a lane type
@@ -299,7 +305,9 @@ __host__ __device__ constexpr int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 // Same with one spare slot per P (P = the radix of the first pass, whose
 // stride-P writes it spreads over the banks); padded_len(n) covers it.
-template <int P> __host__ __device__ constexpr int pidx_p(int i) { return i + i / P; }
+// (an unsigned division by the power of two P: one shift, and offsets that
+// are multiples of P fold into the instruction's immediate)
+template <int P> __host__ __device__ constexpr int pidx_p(int i) { return i + (int)((unsigned)i / (unsigned)P); }
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 __host__ __device__ constexpr bool is_pow2_dev(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -331,7 +339,8 @@ __host__ __device__ constexpr int fft_twiddle_entries(int LF, int emax = 16) { r
 // thread group; C2: two FFTs with the same twiddles, one per packed lane).
 // `s` points at padded_len(LF) shared elements (SmemT<V>) owned by this FFT;
 // `t` is the thread's index in [0, T); `tw` is the float64-generated twiddle
-// table of this LF (TwEntry<V>; forward angles, the inverse conjugates on
+// table of this LF (TwEntry<V> by default; TWT = float4 reads the packed
+// pairs (c, c, s, s) for C2 lanes; forward angles, the inverse conjugates on
 // the fly).  Every thread of the CTA must call run() (it contains
 // __syncthreads), including threads with dummy data.
 #ifndef SPEC_TW_CHUNK
@@ -339,9 +348,9 @@ __host__ __device__ constexpr int fft_twiddle_entries(int LF, int emax = 16) { r
 #endif
 constexpr int kTwChunk = SPEC_TW_CHUNK;   // twiddles loaded per compiler fence
 
-template <int LF, bool INV, class V = float2, int EMAX = 16> struct BlockFFT {
+template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typename TwEntry<V>::type> struct BlockFFT {
     using S = FFTShape<LF, EMAX>;
-    using TW = typename TwEntry<V>::type;
+    using TW = TWT;
     using SM = typename SmemT<V>::type;
     static constexpr int E = S::E;
     static constexpr int T = S::T;

@@ -438,6 +438,130 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2(FftArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Two-lane kernel compiled for one (LZ, R) with one CTA per group of traces
+// (C == 1): lanes a and b carry residues g and g + R/2 of one trace, as in
+// k_fft_real_padded2, but every trace size, step and offset is a
+// compile-time constant, and the tables are stored in the packed pair
+// layout the two-lane arithmetic reads without register shuffles:
+//   pre4[g][m] = (wa.x, wb.x, wa.y, wb.y), wa = w_H^{g m}, wb = w_H^{(g+R/2) m}
+//   tw4[e]     = (c, c, s, s) for the BlockFFT<LZ> twiddle c + j s.
+// Table layout after the generic part (fixed_table_offsets): see below.
+__host__ __device__ constexpr int fixed_generic_entries(int LZ, int R) {
+    return R * (LZ / 16) + R * 16 + R * LZ / 2 + 1;
+}
+// float4 index of pre4 and of tw4 in a table that starts 16-byte aligned
+__host__ __device__ constexpr int fixed_pre4_index(int LZ, int R) { return (fixed_generic_entries(LZ, R) + 1) / 2; }
+__host__ __device__ constexpr int fixed_tw4_index(int LZ, int R) { return fixed_pre4_index(LZ, R) + (R / 2) * LZ; }
+
+// z (a packed sample pair) times the two lanes' pre-twiddles
+__device__ __forceinline__ C2 pretwiddle2(float2 z, float4 w) {
+    const float2 zx = make_float2(z.x, z.x), zy = make_float2(z.y, z.y);
+    const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+    return C2{sub2(mul2(zx, wr), mul2(zy, wi)), fma2(zx, wi, mul2(zy, wr))};
+}
+
+// X[k], X[H - k] from A = Z[k], B = Z[H - k], w = e^{-j pi k/H}/2 (the 1/2
+// of the real-input unpack folded into w), 0 < k < H/2
+template <int H>
+__device__ __forceinline__ void unpack_pair_half(float2* Xr, int k, float2 A, float2 B, float2 w) {
+    const float sx = A.x + B.x, sy = A.y - B.y;
+    const float dx = A.x - B.x, dy = A.y + B.y;
+    const float p = fmaf(w.x, dx, -w.y * dy), q = fmaf(w.x, dy, w.y * dx);   // w (A - conj B)
+    Xr[k] = make_float2(fmaf(0.5f, sx, q), fmaf(0.5f, sy, -p));
+    Xr[H - k] = make_float2(fmaf(0.5f, sx, -q), fmaf(-0.5f, sy, -p));
+}
+
+template <int LZ, int R>
+__global__ void __launch_bounds__(256, 2) k_fft_real_padded2r(FftArgs a) {
+    constexpr int T = LZ / 16, E = 16, G = R / 2, PT = G * T;
+    constexpr int F = PT >= 256 ? 1 : 256 / PT;
+    constexpr int H = R * LZ;
+    constexpr int TS = padded_len(H) + 2;          // float2 per trace (even: float4 views)
+    using FFT = BlockFFT<LZ, false, C2, 16, float4>;
+    static_assert(PT * E == H / 2, "one CTA holds the trace's residue pairs");
+    extern __shared__ float4 smem4[];
+
+    const int tid = threadIdx.x;
+    const int f = tid / PT;
+    const int lt = tid - f * PT;
+    const int gl = lt / T;
+    const int t = lt - gl * T;
+    const int64_t b = (int64_t)blockIdx.x * F + f;
+    const bool live = b < a.batch;
+    int n = a.n;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+    }
+    float2* zs = reinterpret_cast<float2*>(smem4) + f * TS;
+    float4* s = reinterpret_cast<float4*>(zs) + gl * padded_len(LZ);
+    const float4* tab4 = reinterpret_cast<const float4*>(a.tab);
+
+    C2 v[E];
+    {
+        const float4* w4 = tab4 + fixed_pre4_index(LZ, R) + gl * LZ + t;
+        const float* xr = a.x + xo;
+        if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
+            const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
+#pragma unroll
+            for (int i = 0; i < E; ++i) v[i] = pretwiddle2(__ldg(x2 + T * i), __ldg(w4 + T * i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int m = t + T * i;
+                float re = 0.f, im = 0.f;
+                if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+                if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+                v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
+            }
+        }
+    }
+    FFT::run(v, s, t, tab4 + fixed_tw4_index(LZ, R));
+
+    // Z[R q + r] for the lanes' residues, q = t + T i, in natural order
+    __syncthreads();
+    {
+        constexpr int ST = 17 * (T * R / 16);      // pidx step of q -> q + T
+        static_assert((T * R) % 16 == 0, "constant staging step");
+        float2* pa = zs + pidx(t * R + gl);
+        float2* pb = zs + pidx(t * R + gl + G);
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            pa[ST * i] = lane_a(v[i]);
+            pb[ST * i] = lane_b(v[i]);
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+
+    // unpack the pairs (k, H - k), k = lt + PT j (j < E) covering [0, H/2),
+    // plus k = H/2; the twiddle w_{2H}^k/2 = (w^{lt}/2) w^{PT j}
+    float2* Xr = a.X + Xo;
+    const float2* wp = a.tab + R * T + R * E;
+    const float2 w0 = cscale(__ldg(wp + lt), 0.5f);
+    constexpr int STEP = PT + PT / 16;
+    static_assert(PT % 16 == 0, "constant unpack step");
+    const float2* za = zs + pidx(lt);
+    const float2* zb = zs + pidx(H - lt);
+    if (lt == 0) {
+        // k = 0: X[0] = Re Z0 + Im Z0, X[H] = Re Z0 - Im Z0; k = H/2: conj
+        const float2 Z0 = zs[0];
+        Xr[0] = make_float2(Z0.x + Z0.y, 0.f);
+        Xr[H] = make_float2(Z0.x - Z0.y, 0.f);
+        const float2 Zh = zs[pidx(H / 2)];
+        Xr[H / 2] = make_float2(Zh.x, -Zh.y);
+    } else {
+        unpack_pair_half<H>(Xr, lt, za[0], zb[0], w0);
+    }
+#pragma unroll
+    for (int j = 1; j < E; ++j)
+        unpack_pair_half<H>(Xr, lt + PT * j, za[STEP * j], zb[-STEP * j], cmul(w0, __ldg(wp + PT * j)));
+}
+
+// ---------------------------------------------------------------------------
 // Pruned complex FFT with a rotated store: Y[(j + shift) mod K] = U[j],
 // U = FFT_K of u[0 .. nin-1] zero-padded to K.  The same residue
 // decomposition as above (R = K/LZ pre-twiddled LZ-point FFTs, a cluster of
@@ -658,6 +782,20 @@ static FftKernel fft_kernel2_for(int LZ) {
     }
 }
 
+// (LZ, R) pairs with a compiled fixed two-lane kernel.  Measured on GB300:
+// 65536 traces of 1024 samples to 8192 points (LZ 512, R 8) 801 -> 775 us;
+// 4096 traces of 2048 samples to 16384 points (LZ 1024, R 8) 109 -> 113 us,
+// so that size keeps the generic two-lane kernel.
+static FftKernel fft_kernel_fixed_for(int LZ, int R) {
+#define SPEC_FIXED(lz, r) if (LZ == lz && R == r) return k_fft_real_padded2r<lz, r>;
+    SPEC_FIXED(256, 8) SPEC_FIXED(512, 8)
+    SPEC_FIXED(512, 4) SPEC_FIXED(1024, 4) SPEC_FIXED(2048, 4)
+    SPEC_FIXED(256, 16) SPEC_FIXED(512, 16)
+    SPEC_FIXED(1024, 2) SPEC_FIXED(2048, 2) SPEC_FIXED(4096, 2)
+#undef SPEC_FIXED
+    return nullptr;
+}
+
 static FftKernel fft_kernel_for(int LZ, int emax) {
     if (emax == 32) {
         switch (LZ) {
@@ -737,6 +875,7 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     // distributed shared memory
     p->paired = C > 1 && (p->Rc % 2 == 0 || (p->Rc == 1 && R == 2));
     p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096 && p->emax == 16 && !p->paired && (p->Rc / 2) * T <= 256;
+    p->fixed = p->dual && C == 1 && fft_kernel_fixed_for((int)LZ, (int)R) != nullptr;
     const int per_trace = p->dual ? (p->Rc / 2) * T : p->Rc * T;
     p->F = 1;
     if (C == 1) {
@@ -753,7 +892,12 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     return true;
 }
 
-int fft_table_entries(const FftPlan& p) { return p.R * p.T + p.R * p.E + p.H / 2 + 1; }
+int fft_table_entries(const FftPlan& p) {
+    const int generic = p.R * p.T + p.R * p.E + p.H / 2 + 1;
+    if (!p.fixed) return generic;
+    // + packed pre-twiddles [R/2][LZ] and BlockFFT<LZ> twiddles, float4 each
+    return 2 * (fixed_tw4_index(p.LZ, p.R) + fft_twiddle_entries(p.LZ));
+}
 
 void fft_fill_table(const FftPlan& p, float2* host) {
     const double two_pi = 6.283185307179586476925286766559;
@@ -768,6 +912,29 @@ void fft_fill_table(const FftPlan& p, float2* host) {
     for (int r = 0; r < p.R; ++r)
         for (int i = 0; i < p.E; ++i) *o++ = w((int64_t)r * p.T * i, H);
     for (int64_t k = 0; k <= H / 2; ++k) *o++ = w(k, 2 * H);
+    if (!p.fixed) return;
+    // packed two-lane pre-twiddles: lanes g and g + R/2 at m
+    float4* o4 = reinterpret_cast<float4*>(host) + fixed_pre4_index(p.LZ, p.R);
+    for (int g = 0; g < p.R / 2; ++g)
+        for (int m = 0; m < p.LZ; ++m) {
+            const float2 wa = w((int64_t)g * m, H), wb = w((int64_t)(g + p.R / 2) * m, H);
+            *o4++ = make_float4(wa.x, wb.x, wa.y, wb.y);
+        }
+    // BlockFFT<LZ> twiddles of the radix-16 layout as packed pairs (c, c, s, s)
+    const int lg = ilog2(p.LZ), npb = lg / 4, rem = 1 << (lg % 4);
+    const int npass = npb + (rem > 1 ? 1 : 0);
+    float4* t4 = reinterpret_cast<float4*>(host) + fixed_tw4_index(p.LZ, p.R);
+    int ns = 1;
+    for (int q = 0; q < npass; ++q) {
+        const int Rq = q < npb ? 16 : rem;
+        if (q >= 1)
+            for (int r = 1; r < Rq; ++r)
+                for (int k = 0; k < ns; ++k) {
+                    const float2 e = w((int64_t)r * k, (int64_t)ns * Rq);
+                    t4[ns - 16 + (r - 1) * ns + k] = make_float4(e.x, e.x, e.y, e.y);
+                }
+        ns *= Rq;
+    }
 }
 
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
@@ -779,6 +946,21 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
         return cudaGetLastError();
     }
     const bool dual = p.dual && lanes != 1;
+    if (dual && p.fixed) {
+        // compile-time (LZ, R): 256 threads, 256 / (R/2 LZ/16) traces per CTA
+        FftKernel kf = fft_kernel_fixed_for(p.LZ, p.R);
+        const int PT = (p.R / 2) * (p.LZ / 16);
+        const int F = std::max(1, 256 / PT);
+        const size_t smem = (size_t)F * (padded_len(p.H) + 2) * sizeof(float2);
+        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        FftArgs a = {};
+        a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
+        a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = 1; a.F = F;
+        a.tab = tab; a.X = X; a.ld_X = ld_X; a.items = items;
+        kf<<<(unsigned)((batch + F - 1) / F), F * PT, smem, st>>>(a);
+        return cudaGetLastError();
+    }
     FftKernel k = dual ? fft_kernel2_for(p.LZ) : fft_kernel_for(p.LZ, p.emax);
     if (!k) return cudaErrorInvalidValue;
     FftArgs a = {};

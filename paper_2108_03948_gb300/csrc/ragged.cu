@@ -334,7 +334,7 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
                 cand.fp.emax = emax;
                 cand.fp.E = std::min(emax, cand.fp.LZ);
                 cand.fp.T = cand.fp.LZ / cand.fp.E;
-                if (emax == 32) cand.fp.dual = false;
+                if (emax == 32) cand.fp.dual = cand.fp.fixed = false;
                 if (lanes == 2 && !cand.fp.dual) continue;
                 cand.lanes = lanes;
                 if (emax != k.fp.emax && ctx_plan_table(c, 0, cand.fp, &cand.tab) != SPEC_OK) continue;

@@ -251,7 +251,7 @@ spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, 
 // complex FFT (kind 1), built on the host in float64 and cached.
 spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab) {
     for (auto& it : c->fft)
-        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax) {
+        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax && it.fixed == (kind == 0 && p.fixed)) {
             *tab = it.tab;
             return SPEC_OK;
         }
@@ -260,6 +260,7 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     ne.H = p.H;
     ne.LZ = p.LZ;
     ne.emax = p.emax;
+    ne.fixed = kind == 0 && p.fixed;
     std::vector<float2> host((size_t)(kind == 0 ? fft_table_entries(p) : c2c_table_entries(p)));
     if (kind == 0) fft_fill_table(p, host.data());
     else c2c_fill_table(p, host.data());

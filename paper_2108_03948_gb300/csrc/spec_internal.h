@@ -54,6 +54,7 @@ struct FftPlan {
     int F = 0;      // traces per CTA (C == 1 only)
     bool dual = false;  // two residues per thread (packed lanes)
     bool paired = false;  // C > 1 CTAs own residue pairs {r, R - r}: no cluster, local unpack
+    bool fixed = false;   // two-lane kernel compiled for this (LZ, R) with packed tables (C == 1)
     int emax = 16;      // elements per thread (16 or 32: radix of the passes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
@@ -61,8 +62,9 @@ struct FftPlan {
 };
 // Returns false (with a reason) if the size needs a path the library lacks.
 bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why);
-// Per-plan twiddles (pre-twiddle factors and the unpack twiddle), float64 on
-// the host, rounded to float.
+// Per-plan twiddles (pre-twiddle factors and the unpack twiddle; with
+// `fixed` also the packed two-lane pre-twiddles and BlockFFT twiddles),
+// float64 on the host, rounded to float.
 int fft_table_entries(const FftPlan& p);
 void fft_fill_table(const FftPlan& p, float2* host);
 // lanes: 1 forces one FFT per thread group, otherwise the two-lane kernel is
