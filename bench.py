@@ -648,8 +648,10 @@ class Ragged:
             self.bytes[name] = float(sum(c[1] for c in cost))
             self.flops[name] = float(sum(c[2] for c in cost))
             self.offs[name] = (oo, nb)
-            self.descs[name] = (kind, [spec.spec_desc(int(xo[i]), it.n, int(oo[i]), it.f1, it.f2, it.n_fft, it.m,
-                                                      it.d, int(to[i]), it.n_taps) for i, it in enumerate(self.items)])
+            # marshalled once: the timed calls pass the ready array
+            self.descs[name] = (kind, spec.desc_array(
+                [spec.spec_desc(int(xo[i]), it.n, int(oo[i]), it.f1, it.f2, it.n_fft, it.m, it.d, int(to[i]),
+                                it.n_taps) for i, it in enumerate(self.items)]))
             self.out[name] = torch.empty(int(nb.sum()), dtype=torch.complex64, device=dev)
         self.bound = {"fft": "hbm", "czt": "alu", "zoom": None}
         self.name = W2_NAME if len(self.items) == 10000 else \
@@ -827,6 +829,16 @@ def measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, scaling):
            "kernels": kern, "roofline": roofline_of(kern, wl, peaks), "gpu_launches_per_step": launches,
            "e2e": {"value": e2e_val, "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "steps": e2e_steps, "ms_per_step": e2e_ms, "max_abs_diff_vs_device_path": e2e_diff}}
+    if wl == 2:
+        # which form each transform's plan runs (the persistent work queue or
+        # the per-shape launches), as timed when the plan was built
+        forms = {}
+        for name, (kind, d) in W.descs.items():
+            info = spec.spec_ragged_plan_info(ctx, kind, d, synth.FS)
+            if info is not None:
+                forms[name] = {"work_queue": info[0], "queue_us": round(info[1], 1),
+                               "per_shape_us": round(info[2], 1)}
+        res["ragged_plan"] = forms
     cpu = None
     if want_cpu:
         cpu, errs, key = W.cpu_leg()
@@ -978,8 +990,9 @@ def run_ours(args):
         "workloads": others,
         "wall_s": wall,
     }
-    if "czt_gemm_vs_bluestein" in h:
-        line["czt_gemm_vs_bluestein"] = h["czt_gemm_vs_bluestein"]
+    for key in ("czt_gemm_vs_bluestein", "ragged_plan"):
+        if key in h:
+            line[key] = h[key]
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

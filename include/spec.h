@@ -50,8 +50,17 @@ typedef enum {
 } spec_status;
 
 /* How spec_czt evaluates the chirp-z transform.
- *   SPEC_CZT_AUTO          the library picks (Bluestein unless a GEMM form is
- *                          faster at the 1e-5 accuracy bar).
+ *   SPEC_CZT_AUTO          the library picks by measurement: the first call
+ *                          with a given (N, M, batch rounded up to a power of
+ *                          two) runs Bluestein and SPEC_CZT_GEMM_F16X3 on a
+ *                          probe batch of synthetic traces on the device,
+ *                          admits the product only if its spectra agree with
+ *                          Bluestein's to 1e-5 relative L2 each, and keeps
+ *                          the faster (synchronises the stream; the decision
+ *                          is remembered in the context and, if the
+ *                          environment variable SPEC_AUTOTUNE_CACHE names a
+ *                          file when the context is created, in that file --
+ *                          see spec_czt_auto_mode).
  *   SPEC_CZT_BLUESTEIN     FP32 Bluestein: chirp, FFT convolution, chirp
  *                          (Section 2.3, Eq. 13-15).
  *   SPEC_CZT_GEMM_F16X3    Eq. 11 as the product x Z^T, Z[k][n] = z_k^{-n},
@@ -62,13 +71,18 @@ typedef enum {
  *                          counterpart (it uses Bluestein only).
  *   SPEC_CZT_GEMM_F16X1    the same with one FP16 product: relative error
  *                          about 1e-3 (below the 1e-5 bar; for screening).
+ *   SPEC_CZT_GEMM_BF16X1   one BF16 product (x and Z rounded once to BF16,
+ *                          FP32 accumulation): the single-term BF16 error,
+ *                          about 3e-3 relative (below the 1e-5 bar; reported
+ *                          beside the split form, not an accurate mode).
  * The GEMM modes cache Z (2 x 2M x ceil64(N) FP16) per (N, M, f1/fs,
  * step/fs) and use a workspace of 4 bytes per input sample.             */
 typedef enum {
     SPEC_CZT_AUTO = 0,
     SPEC_CZT_BLUESTEIN = 1,
     SPEC_CZT_GEMM_F16X3 = 2,
-    SPEC_CZT_GEMM_F16X1 = 3
+    SPEC_CZT_GEMM_F16X1 = 3,
+    SPEC_CZT_GEMM_BF16X1 = 4
 } spec_czt_mode;
 
 typedef struct spec_ctx spec_ctx;
@@ -224,6 +238,33 @@ SPEC_API spec_status spec_czt_static(const float* x, int64_t batch, int64_t n, i
                                      float* X, int64_t ld_X, void* stream);
 
 /*
+ * The explicit mode SPEC_CZT_AUTO stands for at (batch, n, m): taken from the
+ * context, or from the SPEC_AUTOTUNE_CACHE file read at context creation, or
+ * measured now on a device probe batch (synchronises `stream`).  This is the
+ * autotuner the paper's cost comparison of Section 2.3 (after Eq. 25) and
+ * Section 4 motivates: the faster exact evaluation of Eq. 11 per shape.
+ * *mode receives SPEC_CZT_BLUESTEIN or SPEC_CZT_GEMM_F16X3; a following
+ * spec_czt call with that mode computes bit for bit what SPEC_CZT_AUTO does.
+ */
+SPEC_API spec_status spec_czt_auto_mode(spec_ctx* ctx, int64_t batch, int64_t n, double fs, double f1, double f2,
+                                        int64_t m, int* mode, void* stream);
+
+/*
+ * The decision cache file (host only, no device needed; no counterpart in
+ * the paper).  One JSON object {"format": "spec-autotune-1", "device": tag,
+ * "entries": {key: value}}; keys and values use only letters, digits and
+ * "_.:=| -".  spec_tune_cache_store adds or replaces one entry, keeping the
+ * file's other entries only if they were written for the same device tag
+ * and format (a file from another device or format is replaced), through a
+ * temporary file and a rename; returns 0, or -1 if the file cannot be
+ * written.  spec_tune_cache_lookup returns 1 and copies the value (truncated
+ * to cap - 1 characters) if the file exists, parses, has this device tag and
+ * format, and holds the key; else 0.
+ */
+SPEC_API int spec_tune_cache_store(const char* path, const char* device, const char* key, const char* value);
+SPEC_API int spec_tune_cache_lookup(const char* path, const char* device, const char* key, char* value, int cap);
+
+/*
  * Ragged batches: many traces, each with its own length, band, point count,
  * decimation and taps, in one call.  Each descriptor is one independent
  * spec_fft / spec_czt / spec_zoom problem on one trace (the paper's three
@@ -238,10 +279,14 @@ SPEC_API spec_status spec_czt_static(const float* x, int64_t batch, int64_t n, i
  * array is host memory and is copied.  Outputs of different descriptors
  * must not overlap (not checked).
  * The first call with a descriptor list synchronises `stream`, builds a plan
- * (per-trace tables, class grouping, variant autotuning by timing, one CUDA
- * graph with a launch per class) and caches it in the context; a repeated
- * call with identical descriptors and pools is one graph launch,
- * asynchronous on `stream`.  Every descriptor is validated before anything
+ * and caches it in the context: per kind one persistent launch over a work
+ * queue of units (a few traces of one shape, or part of one long trace),
+ * largest first, popped by one CTA per SM; traces beyond the queue kernels'
+ * sizes (padded-FFT residue FFTs above 4096 points, Zoom N_FFT/d above
+ * 16384) run as per-shape launches in the same graph; the alternatives a
+ * plan admits are timed and the fastest kept.  A repeated call with
+ * identical descriptors and pools is one graph launch, asynchronous on
+ * `stream`.  Every descriptor is validated before anything
  * runs (SPEC_EINVAL / SPEC_EUNSUPPORTED with the descriptor's index in
  * spec_last_error).
  */
@@ -263,11 +308,25 @@ SPEC_API spec_status spec_ragged(spec_ctx* ctx, int kind, const spec_desc* descs
                                  const float* x_pool, const float* taps_pool, float* X_pool, void* stream);
 
 /* Kernel launches one replay of the cached plan for these descriptors makes
- * (one per class of traces, plus one FIR launch for Zoom FFTs too large for
- * one CTA), or -1 if the context holds no such plan.  Library bookkeeping;
- * the paper has no counterpart. */
+ * (the work-queue launch if the plan uses it, one per remaining class of
+ * traces, plus one FIR launch for Zoom FFTs too large for one CTA), or -1 if
+ * the context holds no such plan.  Library bookkeeping; the paper has no
+ * counterpart.  (SPEC_RAGGED_QUEUE=1 or 0 in the environment when a context
+ * is created makes its plans always, or never, use the work queue.) */
 SPEC_API int64_t spec_ragged_launches(const spec_ctx* ctx, int kind, const spec_desc* descs, int64_t count,
                                       double fs);
+
+/*
+ * How the cached plan for these descriptors runs (no counterpart in the
+ * paper; host only, no device work): returns 1 if its graph launches the
+ * persistent work queue, 0 if the per-shape launches were faster when the
+ * plan was built (both forms are timed then; their times in microseconds go
+ * to *t_queue_us and *t_classes_us, 0 where the plan has no queue), -1 if
+ * the context holds no plan for these descriptors.  Either pointer may be
+ * NULL.
+ */
+SPEC_API int spec_ragged_plan_info(const spec_ctx* ctx, int kind, const spec_desc* descs, int64_t count, double fs,
+                                   float* t_queue_us, float* t_classes_us);
 
 /* ---- host-only helpers (pure functions, no CUDA calls) ----------------- */
 

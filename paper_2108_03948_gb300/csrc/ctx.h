@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -24,7 +25,7 @@ struct CztEntry {
 struct FftEntry {
     int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables, 2: multi-pass twiddles (H = period log2)
     int H = 0, LZ = 0, emax = 16;
-    bool fixed = false;  // kind 0 with the packed tables of the fixed two-lane kernel
+    int layout = 0;      // kind 0: generic (0), fixed two-lane (1) or cluster (2) table layout
     float2* tab = nullptr;
 };
 
@@ -32,6 +33,7 @@ struct GemmZEntry {       // cached FP16 split of Z for the GEMM chirp-z
     int64_t n = 0, m = 0;
     uint64_t A = 0, B = 0;
     double a0 = 1.0, w0 = 1.0;           // contour radius parameters (1, 1: the unit circle)
+    bool bf16 = false;                   // one BF16 part (SPEC_CZT_GEMM_BF16X1) instead of the FP16 split
     int* col_pow = nullptr;              // off the circle: per-bin column exponents (inside z)
     void* z = nullptr;
     cudaEvent_t ready = nullptr;
@@ -47,6 +49,10 @@ struct spec_ctx {
     float2* block_tw = nullptr;          // BlockFFT twiddles of every size
     int lanes = 0;                       // 0: per transform (two packed lanes for the padded FFT, one for the
                                          // chirp-z and Zoom: measured fastest); 1 or 2: forced everywhere
+    bool fft_cluster = false;            // SPEC_FFT_CLUSTER=1: long traces on k_fft_real_cluster
+    int ragged_queue = -1;               // SPEC_RAGGED_QUEUE: 1 always / 0 never the work queue, -1 timed
+    std::map<std::string, std::string> tune;   // SPEC_CZT_AUTO decisions ("czt n=.. m=.. b=.." -> mode)
+    std::string tune_path, tune_device;        // SPEC_AUTOTUNE_CACHE file and this device's tag
     std::vector<FftEntry> fft;
     std::vector<CztEntry> czt;
     std::vector<GemmZEntry> gemm_z;
@@ -69,4 +75,13 @@ spec_status ctx_cuda_fail(spec_ctx* c, cudaError_t e, const char* what);
 bool ctx_is_device_ptr(const void* p);
 // Cached per-shape twiddle tables: kind 0 padded real FFT, kind 1 pruned complex FFT.
 spec_status ctx_plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab);
+// autotune.cu: the persisted decision cache and the SPEC_CZT_AUTO decision
+bool tune_file_read(const std::string& path, const std::string& device, std::map<std::string, std::string>* entries);
+bool tune_file_write(const std::string& path, const std::string& device,
+                     const std::map<std::string, std::string>& entries);
+bool tune_file_store(const std::string& path, const std::string& device, const std::string& key,
+                     const std::string& value);
+std::string device_tag(int device);
+spec_status czt_auto_decide(spec_ctx* c, int64_t batch, int64_t n, double fs, double f1, double f2, int64_t m,
+                            int* mode, cudaStream_t st);
 }  // namespace spec

@@ -91,6 +91,24 @@ __device__ __forceinline__ float2 unit_fixed(uint64_t ph, bool negative) {
     return negative ? make_float2(re, -im) : make_float2(re, im);
 }
 
+// Same phase through the hardware sine and cosine (__sincosf, absolute error
+// about 4e-7 for arguments in [-pi, pi], which the fixed-point reduction
+// guarantees), with the same first-order remainder: for chirps evaluated in a
+// kernel, where the library call's cost matters.
+__device__ __forceinline__ float2 unit_fast(uint64_t ph, bool negative) {
+    const int64_t s = (int64_t)ph;
+    const int32_t hi = (int32_t)(s >> 32);
+    const float hf = (float)hi;
+    const int64_t rem = (int64_t)((uint64_t)s - ((uint64_t)(int64_t)hf << 32));
+    const float ang = hf * 1.4629180792671596e-9f;                      // * 2 pi / 2^32
+    const float xr = (float)rem * 1.0842021724855044e-19f * 3.14159265358979f;
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    const float re = fmaf(-xr, sn, cs);
+    const float im = fmaf(xr, cs, sn);
+    return negative ? make_float2(re, -im) : make_float2(re, im);
+}
+
 // e^{sign j 2 pi ph/2^64} evaluated in float64 (table generation only).
 __device__ __forceinline__ float2 unit_fixed_f64(uint64_t ph, bool negative) {
     const double cyc = (double)(int64_t)ph * 5.421010862427522e-20;   // * 2^-64

@@ -449,4 +449,212 @@ cudaError_t czt_ragged_launch(int L, const RaggedItem* items, int64_t count, con
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Ragged batches as one persistent launch (work queue).  Every trace has its
+// own (N, M, band); its Bluestein length L = nextpow2(N + M - 1) <= 16384.
+// A unit of work is 16384/L traces of one L, so every unit holds 16384 FFT
+// points and runs on the same 1024-thread CTA (16 elements per thread, one
+// trace per group of L/16 threads).  The units are sorted by length (largest
+// first) on the host and popped from an atomic counter by persistent CTAs,
+// one per SM.  The chirps of Eq. 13-15 are evaluated in the kernel from the
+// exact 64-bit fixed-point phases (pre[n] = e^{-j2pi(A n + B n^2)}, post[k] =
+// e^{-j2pi B k^2}); only FFT(v)/L, which depends on (N, M, B) alone, comes
+// from a table, one per distinct (N, M, B) of the batch.
+struct CztQueueArgs {
+    const RaggedItem* items;   // tab_off: offset of the trace's FFT(v)/L in vpool
+    const CztUnit* units;
+    int nunits;
+    unsigned* counter;         // zeroed before the launch
+    const float* x;
+    const float2* vpool;
+    float2* X;
+    const float2* tw;          // BlockFFT twiddles of every size (radix-16 layout)
+    const float2* tw32;        // the same for radix-32 passes
+};
+
+constexpr int kCztUnitPoints = 8192;
+constexpr int kCztQueueThreads = kCztUnitPoints / 16;
+// the longest length runs one trace per unit with 32 elements per thread
+template <int L> struct CztQueueShape { static constexpr int EMAX = L > kCztUnitPoints ? 32 : 16; };
+
+// The trace of this thread's group, looked up again from opaque copies of the
+// unit index and thread index, so that nothing but the FFT data stays live
+// across the transforms (64 registers at 1024 threads).
+template <int L>
+__device__ __forceinline__ const RaggedItem* czt_queue_item(const CztQueueArgs& a, int ui, bool* live) {
+    constexpr int T = FFTShape<L, CztQueueShape<L>::EMAX>::T;
+    unsigned tid;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    asm volatile("" : "+r"(ui));
+    const int f = (int)tid / T;
+    const CztUnit u = a.units[ui];
+    *live = f < u.count;
+    return a.items + u.first + (*live ? f : 0);
+}
+
+template <int L>
+__device__ __forceinline__ void czt_queue_unit(const CztQueueArgs& a, int ui, float2* smem) {
+    constexpr int EMAX = CztQueueShape<L>::EMAX;
+    using Fw = BlockFFT<L, false, float2, EMAX>;
+    using Iv = BlockFFT<L, true, float2, EMAX>;
+    constexpr int E = Fw::E, T = Fw::T;
+    constexpr int SL = L + L / EMAX;                      // padded slots of one trace
+    const int f = threadIdx.x / T;
+    const int t = threadIdx.x - f * T;
+    const float2* tw = (EMAX == 32 ? a.tw32 : a.tw) + fft_twiddle_offset(L, EMAX);
+    float2* s = smem + f * SL;
+    // The chirps are evaluated while no FFT data is live in registers: the
+    // chirped input goes through this thread's own slots of the shared
+    // FFT area (read back before the FFT's first barrier), and the inverse
+    // FFT's outputs come back through the same slots.
+    {
+        bool live;
+        const RaggedItem* it = czt_queue_item<L>(a, ui, &live);
+        const float* xr = a.x + it->x_off;
+        const int n = it->n;
+        const uint64_t A = it->A, B = it->B;
+        for (int i = 0; i < E; ++i) {
+            const int nn = t + T * i;
+            const uint64_t q = (uint64_t)nn;
+            s[pidx_p<EMAX>(nn)] = (live && nn < n) ? cscale(unit_fast(A * q + B * (q * q), true), __ldg(xr + nn))
+                                                   : make_float2(0.f, 0.f);
+        }
+    }
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = s[pidx_p<EMAX>(t + T * i)];
+    Fw::run(v, s, t, tw);
+    {
+        bool live;
+        const float2* V = a.vpool + czt_queue_item<L>(a, ui, &live)->tab_off;
+        unsigned tt;
+        asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tt));
+        V += (int)(tt % T);
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = cmul(v[i], __ldg(V + T * i));
+    }
+    int t2 = t;
+    asm volatile("" : "+r"(t2));
+    Iv::run(v, s, t2, tw);
+    unsigned tid;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    const int t3 = (int)(tid % T);
+    float2* s3 = smem + (int)(tid / T) * SL;
+#pragma unroll
+    for (int i = 0; i < E; ++i) s3[pidx_p<EMAX>(t3 + T * i)] = v[i];
+    bool live;
+    const RaggedItem* it = czt_queue_item<L>(a, ui, &live);
+    if (!live) return;
+    float2* Xr = a.X + it->out_off;
+    const int m = it->m;
+    const uint64_t B = it->B;
+    for (int i = 0; i < E; ++i) {
+        const int k = t3 + T * i;
+        const uint64_t q = (uint64_t)k;
+        if (k < m) Xr[k] = cmul(s3[pidx_p<EMAX>(k)], unit_fast(B * (q * q), true));
+    }
+}
+
+__global__ void __launch_bounds__(kCztQueueThreads, 1) k_czt_queue(CztQueueArgs a) {
+    extern __shared__ float2 smem[];
+    __shared__ int s_unit;
+    for (;;) {
+        __syncthreads();                              // the previous unit is done with s_unit and smem
+        if (threadIdx.x == 0) s_unit = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int ui = s_unit;
+        if (ui >= a.nunits) return;
+        switch (a.units[ui].L) {
+            case 16: czt_queue_unit<16>(a, ui, smem); break;
+            case 32: czt_queue_unit<32>(a, ui, smem); break;
+            case 64: czt_queue_unit<64>(a, ui, smem); break;
+            case 128: czt_queue_unit<128>(a, ui, smem); break;
+            case 256: czt_queue_unit<256>(a, ui, smem); break;
+            case 512: czt_queue_unit<512>(a, ui, smem); break;
+            case 1024: czt_queue_unit<1024>(a, ui, smem); break;
+            case 2048: czt_queue_unit<2048>(a, ui, smem); break;
+            case 4096: czt_queue_unit<4096>(a, ui, smem); break;
+            case 8192: czt_queue_unit<8192>(a, ui, smem); break;
+            default: czt_queue_unit<16384>(a, ui, smem); break;
+        }
+    }
+}
+
+// FFT(v)/L of one distinct (N, M, B) per CTA, written at items[b].tab_off of
+// vpool: v[m] = e^{+j2pi B m^2} for m in [-(N-1), M-1], wrapped circularly.
+template <int L>
+__global__ void __launch_bounds__(FFTShape<L>::T) k_czt_vpool(const RaggedItem* keys, float2* vpool, const float2* tw) {
+    using FFT = BlockFFT<L, false>;
+    constexpr int E = FFT::E, T = FFT::T;
+    extern __shared__ float2 smem[];
+    const RaggedItem it = keys[blockIdx.x];
+    const int t = threadIdx.x;
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int idx = t + T * i;
+        int64_t mm = 0;
+        bool nz = true;
+        if (idx < it.m) mm = idx;
+        else if (idx >= L - it.n + 1) mm = (int64_t)idx - L;
+        else nz = false;
+        v[i] = nz ? unit_fixed_f64(it.B * (uint64_t)(mm * mm), false) : make_float2(0.f, 0.f);
+    }
+    FFT::run(v, smem, t, tw);
+    const float inv = 1.0f / (float)L;
+    float2* V = vpool + it.tab_off;
+#pragma unroll
+    for (int i = 0; i < E; ++i) V[t + T * i] = cscale(v[i], inv);
+}
+
+using VPoolKernel = void (*)(const RaggedItem*, float2*, const float2*);
+
+static VPoolKernel vpool_kernel_for(int L) {
+    switch (L) {
+        case 16: return k_czt_vpool<16>;
+        case 32: return k_czt_vpool<32>;
+        case 64: return k_czt_vpool<64>;
+        case 128: return k_czt_vpool<128>;
+        case 256: return k_czt_vpool<256>;
+        case 512: return k_czt_vpool<512>;
+        case 1024: return k_czt_vpool<1024>;
+        case 2048: return k_czt_vpool<2048>;
+        case 4096: return k_czt_vpool<4096>;
+        case 8192: return k_czt_vpool<8192>;
+        case 16384: return k_czt_vpool<16384>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t czt_vpool_build(int L, const RaggedItem* keys, int64_t count, float2* vpool, const float2* tw_base,
+                            cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    VPoolKernel k = vpool_kernel_for(L);
+    if (!k) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)padded_len(L) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)count, std::max(1, L / 16), smem, st>>>(keys, vpool, tw_base + (L <= 16 ? 0 : fft_twiddle_offset(L)));
+    return cudaGetLastError();
+}
+
+size_t czt_queue_smem() { return (size_t)(2 * kCztUnitPoints + 2 * kCztUnitPoints / 32) * sizeof(float2); }
+int czt_queue_unit_traces(int L) { return L >= kCztUnitPoints ? 1 : kCztUnitPoints / L; }
+
+// One persistent launch over the unit list; `counter` must be zero (the
+// caller's graph zeroes it before the launch).
+cudaError_t czt_queue_launch(const RaggedItem* items, const CztUnit* units, int nunits, unsigned* counter,
+                             const float* x_pool, const float2* vpool, const float2* tw_base, const float2* tw32_base,
+                             float2* X_pool, int ctas, cudaStream_t st) {
+    if (nunits == 0) return cudaSuccess;
+    const size_t smem = czt_queue_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_czt_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    CztQueueArgs a = {};
+    a.items = items; a.units = units; a.nunits = nunits; a.counter = counter;
+    a.x = x_pool; a.vpool = vpool; a.X = X_pool; a.tw = tw_base; a.tw32 = tw32_base;
+    k_czt_queue<<<(unsigned)std::max(1, std::min(ctas, nunits)), kCztQueueThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace spec

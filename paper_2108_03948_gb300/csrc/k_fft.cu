@@ -562,6 +562,450 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2r(FftArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Traces too long for one CTA (R/2 residue pairs of LZ/16 threads exceed 256
+// threads): a thread-block cluster of C CTAs per trace, each CTA computing
+// 256/(LZ/16) residue pairs, and the spectrum assembled in the CTAs' shared
+// memory so that every HBM store is a contiguous run.
+//
+// Pair g >= 1 holds residues g and R - g.  Lane a transforms z[m] w_H^{g m};
+// lane b transforms conj(z[m]) w_H^{g m}, whose LZ-point FFT at q is
+// conj(Z[H - (R q + g)]) (the DFT of a conjugated sequence is the conjugated,
+// index-reversed DFT, and w_H^{R m} = w_LZ^m shifts that reversal to
+// LZ - 1 - q).  So after the FFT each thread holds, at every q, both members
+// A = Z[k], B' = conj Z[H - k] of its unpack pairs (k, H - k), k = R q + g,
+// and forms X[k] and X[H - k] in registers.  Pair 0 holds residues 0 and
+// R/2, each its own mirror (Z[R q] pairs with Z[R (LZ - q)], Z[R q + R/2]
+// with Z[R (LZ - 1 - q) + R/2]); it exchanges through its own shared memory
+// and forms X[R q] and X[R q + R/2].
+//
+// CTA c of the cluster owns X[8192 c .. 8192 c + 8191] (the last one also
+// X[H]): every output is stored once into its owner's shared memory
+// (distributed shared memory; padded index o + o/8, which keeps the stride-R
+// stores of a warp on distinct banks), and after a cluster barrier each CTA
+// writes its run to HBM with coalesced stores.
+//
+// Table (float2 units): [H/2 + 1: w_{2H}^k] [pad] [pre: R/2 rows of LZ:
+// row 0 w_H^{(R/2) m}, row g w_H^{g m}] [BlockFFT<LZ> twiddles (c, c, s, s)].
+constexpr int kClusterRun = 8192;          // outputs owned by one CTA
+__host__ __device__ constexpr int pidx8(int o) { return o + (o >> 3); }
+__host__ __device__ constexpr int cluster_pre_offset(int H) { return ((H / 2 + 1) + 1) & ~1; }
+__host__ __device__ constexpr int cluster_tw4_index(int H) { return (cluster_pre_offset(H) + H / 2) / 2; }
+
+// X[k] from A = Z[k] and Bc = conj Z[H - k], wh = e^{-j pi k/H}/2
+__device__ __forceinline__ float2 unpack_fwd(float2 A, float2 Bc, float2 wh) {
+    const float sx = A.x + Bc.x, sy = A.y + Bc.y;     // A + conj B
+    const float dx = A.x - Bc.x, dy = A.y - Bc.y;     // A - conj B
+    const float p = fmaf(wh.x, dx, -wh.y * dy), q = fmaf(wh.x, dy, wh.y * dx);
+    return make_float2(fmaf(0.5f, sx, q), fmaf(0.5f, sy, -p));
+}
+// X[H - k] from the same A, Bc and wh (conj of the mirrored formula)
+__device__ __forceinline__ float2 unpack_mirror(float2 A, float2 Bc, float2 wh) {
+    const float sx = A.x + Bc.x, sy = A.y + Bc.y;
+    const float dx = A.x - Bc.x, dy = A.y - Bc.y;
+    const float p = fmaf(wh.x, dx, -wh.y * dy), q = fmaf(wh.x, dy, wh.y * dx);
+    return make_float2(fmaf(0.5f, sx, -q), fmaf(-0.5f, sy, -p));
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+template <int LZ, int R>
+__global__ void __launch_bounds__(256, 2) k_fft_real_cluster(FftArgs a) {
+    constexpr int T = LZ / 16, E = 16, PPC = 256 / T, NP = R / 2, C = NP / PPC;
+    constexpr int H = R * LZ;
+    static_assert(C >= 2 && C <= 8, "a portable cluster");
+    static_assert(H / C == kClusterRun, "each CTA owns 8192 outputs");
+    using FFT = BlockFFT<LZ, false, C2, 16, float4>;
+    extern __shared__ float4 smem4[];
+
+    const int tid = threadIdx.x;
+    const int gl = tid / T;
+    const int t = tid - gl * T;
+    const int c = (int)cluster_rank();
+    const int g = c * PPC + gl;                      // residue pair of this thread group
+    const int64_t b = (int64_t)(blockIdx.x / C);     // one trace per cluster
+    const bool live = b < a.batch;
+    int n = a.n;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+    }
+    float4* s = smem4 + gl * padded_len(LZ);
+    const float2* wk = a.tab;                                     // w_{2H}^k, k <= H/2
+    const float2* pre = a.tab + cluster_pre_offset(H) + g * LZ;
+    const float4* tw4 = reinterpret_cast<const float4*>(a.tab) + cluster_tw4_index(H);
+
+    // 1. packed, pre-twiddled input (lane b conjugated for pairs g >= 1)
+    C2 v[E];
+    {
+        const float* xr = a.x + xo;
+        const bool full = live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float2 z;
+            if (full) {
+                z = __ldg(reinterpret_cast<const float2*>(xr) + m);
+            } else {
+                z.x = (live && 2 * m < n) ? __ldg(xr + 2 * m) : 0.f;
+                z.y = (live && 2 * m + 1 < n) ? __ldg(xr + 2 * m + 1) : 0.f;
+            }
+            const float2 w = __ldg(pre + m);
+            if (g != 0) {
+                const float P = z.x * w.x, Q = z.y * w.y, S = z.x * w.y, U = z.y * w.x;
+                v[i] = C2{make_float2(P - Q, P + Q), make_float2(S + U, S - U)};
+            } else {
+                v[i] = C2{make_float2(z.x, fmaf(z.x, w.x, -z.y * w.y)), make_float2(z.y, fmaf(z.x, w.y, z.y * w.x))};
+            }
+        }
+    }
+    FFT::run(v, s, t, tw4);
+
+    // 2. pair 0: stage Z[R q] and Z[R q + R/2] (natural order in q)
+    __syncthreads();
+    float2* z0 = reinterpret_cast<float2*>(s);
+    float2* z4 = z0 + padded_len(LZ);
+    if (g == 0) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            z0[pidx(t + T * i)] = lane_a(v[i]);
+            z4[pidx(t + T * i)] = lane_b(v[i]);
+        }
+    }
+    __syncthreads();
+
+    // 3. outputs in registers: out[2 i] at k0_i, out[2 i + 1] at k1_i
+    float2 out[2 * E];
+    const float2 wb0 = cscale(__ldg(wk + R * t + g), 0.5f);
+    const float2 wb4 = cscale(__ldg(wk + R * t + R / 2), 0.5f);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const float ci = i <= 8 ? cos_pi16(i) : -cos_pi16(16 - i);
+        const float si = i <= 8 ? cos_pi16(8 - i) : cos_pi16(i - 8);
+        const float2 ei = make_float2(ci, -si);                  // e^{-j pi i/16}
+        const int q = t + T * i;
+        if (g != 0) {
+            const float2 wh = cmul(wb0, ei);
+            out[2 * i] = unpack_fwd(lane_a(v[i]), lane_b(v[i]), wh);
+            out[2 * i + 1] = unpack_mirror(lane_a(v[i]), lane_b(v[i]), wh);
+        } else {
+            const float2 A0 = lane_a(v[i]), B0 = z0[pidx((LZ - q) & (LZ - 1))];
+            const float2 A4 = lane_b(v[i]), B4 = z4[pidx(LZ - 1 - q)];
+            out[2 * i] = unpack_fwd(A0, make_float2(B0.x, -B0.y), cmul(wb0, ei));
+            out[2 * i + 1] = unpack_fwd(A4, make_float2(B4.x, -B4.y), cmul(wb4, ei));
+        }
+    }
+    float2 xh = make_float2(0.f, 0.f);                            // X[H] (pair 0, q = 0)
+    if (g == 0 && t == 0) {
+        const float2 Z0 = lane_a(v[0]);
+        xh = make_float2(Z0.x - Z0.y, 0.f);
+    }
+
+    // 4. every CTA of the cluster is done with its shared memory: store each
+    //    output into its owner's run
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    float2* run = reinterpret_cast<float2*>(smem4);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int q = t + T * i;
+        const int k0 = g != 0 ? R * q + g : R * q;
+        const int k1 = g != 0 ? H - (R * q + g) : R * q + R / 2;
+        dsmem_store(run, pidx8(k0 & (kClusterRun - 1)), (unsigned)(k0 / kClusterRun), out[2 * i]);
+        dsmem_store(run, pidx8(k1 & (kClusterRun - 1)), (unsigned)(k1 / kClusterRun), out[2 * i + 1]);
+    }
+    if (g == 0 && t == 0) dsmem_store(run, pidx8(kClusterRun), (unsigned)(C - 1), xh);
+    cl.sync();
+
+    // 5. coalesced run to HBM
+    if (!live) return;
+    float2* Xr = a.X + Xo + (int64_t)c * kClusterRun;
+#pragma unroll 4
+    for (int o = tid; o < kClusterRun; o += 256) Xr[o] = run[pidx8(o)];
+    if (c == C - 1 && tid == 0) Xr[kClusterRun] = run[pidx8(kClusterRun)];
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches as one persistent launch (work queue).  Every trace has its
+// own N and N_FFT; R = H/LZ residue FFTs of LZ <= 4096 points each.  A unit is
+// the work of one 256-thread CTA (two per SM):
+//   mode 0: F = 256/(R/2 LZ/16) whole traces, two residues per thread as
+//           packed lanes (g, g + R/2), Z staged in natural order and unpacked
+//           with coalesced stores (as k_fft_real_padded2);
+//   mode 1: G = 256/(LZ/16) residue pairs of one trace that does not fit one
+//           CTA.  Pair g >= 1 carries residues g and R - g: lane a transforms
+//           z[m] w_H^{g m}, lane b conj(z[m]) w_H^{g m}, whose FFT at q is
+//           conj Z[H - (R q + g)], so each thread forms X[R q + g] and
+//           X[H - R q - g] in registers.  Pair 0 (residues 0 and R/2, each its
+//           own mirror) exchanges through shared memory.
+// Units are sorted on the host (largest first) and popped from an atomic
+// counter by persistent CTAs, two per SM.
+struct FftQueueArgs {
+    const RaggedItem* items;
+    const FftUnit* units;
+    int nunits;
+    unsigned* counter;
+    const float* x;
+    float2* X;
+    const float2* btw;       // BlockFFT twiddles of every size (radix-16 layout)
+    float2* ws;              // mode 2: per-CTA workspace of ws_per_cta complex values
+    int64_t ws_per_cta;
+};
+
+constexpr int kFftQueueThreads = 256;     // two CTAs per SM at 128 registers
+
+// mode 0: F whole traces per CTA (the two-lane kernel's C == 1 path)
+template <int LZ>
+__device__ __forceinline__ void fft_queue_full(const FftQueueArgs& a, const FftUnit& u, float4* smem4) {
+    using FFT = BlockFFT<LZ, false, C2>;
+    constexpr int E = FFT::E, T = FFT::T;
+    const int R = 1 << u.logR;
+    const int G = R >> 1;
+    const int H = R * LZ;
+    const int PT = G * T;                                      // threads per trace
+    const int TS = padded_len(H) + 2;                          // float2 per trace
+    const int tid = threadIdx.x;
+    const int f = tid / PT;
+    const int lt = tid - f * PT;
+    const int gl = lt / T;
+    const int t = lt - gl * T;
+    const bool live = f < u.count;
+    const RaggedItem it = a.items[u.item + (live ? f : 0)];
+    const int n = it.n;
+    float2* zs = reinterpret_cast<float2*>(smem4) + f * TS;
+    float4* s = reinterpret_cast<float4*>(zs) + gl * padded_len(LZ);
+    const float2* tab = u.tab;
+    const int ra = gl, rb = gl + G;
+
+    C2 v[E];
+    {
+        const C2 wt = c2(__ldg(tab + ra * T + t), __ldg(tab + rb * T + t));
+        const float2* wia = tab + R * T + ra * E;
+        const float2* wib = tab + R * T + rb * E;
+        const float* xr = a.x + it.x_off;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float re = 0.f, im = 0.f;
+            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+            v[i] = cmul(make_float2(re, im), cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
+        }
+    }
+    FFT::run(v, s, t, a.btw + fft_twiddle_offset(LZ));
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int q = (t + T * i) << u.logR;
+        zs[pidx(q + ra)] = lane_a(v[i]);
+        zs[pidx(q + rb)] = lane_b(v[i]);
+    }
+    __syncthreads();
+    if (!live) return;
+    float2* Xr = a.X + it.out_off;
+    const float2* wp = tab + R * T + R * E;
+    const float2 w0 = __ldg(wp + lt);
+    int kj = 0;
+#pragma unroll 4
+    for (int k = lt; k <= H / 2; k += PT, kj += PT)
+        unpack_pair(Xr, k, H, zs[pidx(k)], zs[pidx((H - k) & (H - 1))], cmul(w0, __ldg(wp + kj)));
+}
+
+// mode 1: G residue pairs g0 .. g0 + G - 1 of one trace
+template <int LZ>
+__device__ __forceinline__ void fft_queue_pairs(const FftQueueArgs& a, const FftUnit& u, float4* smem4) {
+    using FFT = BlockFFT<LZ, false, C2>;
+    constexpr int E = FFT::E, T = FFT::T;
+    const int R = 1 << u.logR;
+    const int H = R * LZ;
+    const int tid = threadIdx.x;
+    const int gl = tid / T;
+    const int t = tid - gl * T;
+    const int g = u.g0 + gl;
+    const bool live = gl < u.count;                            // pairs in this unit
+    const RaggedItem it = a.items[u.item];
+    const int n = it.n;
+    float4* s = smem4 + gl * padded_len(LZ);
+    const float2* tab = u.tab;
+    const int ra = live ? g : 0;
+
+    C2 v[E];
+    {
+        // w_H^{r m} = w_H^{r t} w_H^{r T i} for r = g (both lanes; pair 0:
+        // lane a residue 0, lane b residue R/2)
+        const int rw = g == 0 ? R / 2 : ra;
+        const float2 wt = __ldg(tab + rw * T + t);
+        const float2* wi = tab + R * T + rw * E;
+        const float* xr = a.x + it.x_off;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float2 z = make_float2(0.f, 0.f);
+            if (live && 2 * m < n) z.x = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < n) z.y = __ldg(xr + 2 * m + 1);
+            const float2 w = cmul(wt, __ldg(wi + i));
+            if (g != 0) {
+                const float P = z.x * w.x, Q = z.y * w.y, S = z.x * w.y, U = z.y * w.x;
+                v[i] = C2{make_float2(P - Q, P + Q), make_float2(S + U, S - U)};
+            } else {
+                v[i] = C2{make_float2(z.x, fmaf(z.x, w.x, -z.y * w.y)), make_float2(z.y, fmaf(z.x, w.y, z.y * w.x))};
+            }
+        }
+    }
+    FFT::run(v, s, t, a.btw + fft_twiddle_offset(LZ));
+    __syncthreads();
+    float2* z0 = reinterpret_cast<float2*>(s);
+    float2* z4 = z0 + padded_len(LZ);
+    if (g == 0) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            z0[pidx(t + T * i)] = lane_a(v[i]);
+            z4[pidx(t + T * i)] = lane_b(v[i]);
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    float2* Xr = a.X + it.out_off;
+    const float2* wp = tab + R * T + R * E;                    // w_{2H}^k, k <= H/2
+    const float2 wb0 = cscale(__ldg(wp + R * t + g), 0.5f);
+    const float2 wb4 = cscale(__ldg(wp + R * t + R / 2), 0.5f);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        // w_{2H}^{R (t + T i) + g} = w_{2H}^{R t + g} e^{-j pi i/16} (R T = H/16)
+        const float ci = i <= 8 ? cos_pi16(i) : -cos_pi16(16 - i);
+        const float si = i <= 8 ? cos_pi16(8 - i) : cos_pi16(i - 8);
+        const float2 ei = make_float2(ci, -si);
+        const int q = t + T * i;
+        if (g != 0) {
+            const float2 wh = cmul(wb0, ei);
+            Xr[R * q + g] = unpack_fwd(lane_a(v[i]), lane_b(v[i]), wh);
+            Xr[H - (R * q + g)] = unpack_mirror(lane_a(v[i]), lane_b(v[i]), wh);
+        } else {
+            const float2 B0 = z0[pidx((LZ - q) & (LZ - 1))], B4 = z4[pidx(LZ - 1 - q)];
+            Xr[R * q] = unpack_fwd(lane_a(v[i]), make_float2(B0.x, -B0.y), cmul(wb0, ei));
+            Xr[R * q + R / 2] = unpack_fwd(lane_b(v[i]), make_float2(B4.x, -B4.y), cmul(wb4, ei));
+        }
+    }
+    if (g == 0 && t == 0) {
+        const float2 Z0 = lane_a(v[0]);
+        Xr[H] = make_float2(Z0.x - Z0.y, 0.f);
+    }
+}
+
+// mode 2: one whole trace too long for the CTA's shared memory.  The residue
+// pairs (g, g + R/2) run in rounds of G = 512/(LZ/16); each round writes its
+// Z values to this CTA's workspace (H complex values, residue-major, so the
+// stores are coalesced; it stays in L2), and after the last round the CTA
+// unpacks every pair (k, H - k) from the workspace with coalesced stores of X.
+template <int LZ>
+__device__ __forceinline__ void fft_queue_ws(const FftQueueArgs& a, const FftUnit& u, float4* smem4) {
+    using FFT = BlockFFT<LZ, false, C2>;
+    constexpr int E = FFT::E, T = FFT::T;
+    constexpr int G = kFftQueueThreads / T;
+    const int logR = u.logR;
+    const int R = 1 << logR;
+    const int H = R * LZ;
+    const int tid = threadIdx.x;
+    const int gl = tid / T;
+    const int t = tid - gl * T;
+    const RaggedItem it = a.items[u.item];
+    const int n = it.n;
+    float4* s = smem4 + gl * padded_len(LZ);
+    const float2* tab = u.tab;
+    float2* ws = a.ws + (size_t)blockIdx.x * a.ws_per_cta;
+    const float* xr = a.x + it.x_off;
+    for (int g0 = 0; g0 < R / 2; g0 += G) {
+        const int ra = g0 + gl, rb = ra + R / 2;
+        const bool on = ra < R / 2;
+        const int rra = on ? ra : 0, rrb = on ? rb : R / 2;
+        C2 v[E];
+        const C2 wt = c2(__ldg(tab + rra * T + t), __ldg(tab + rrb * T + t));
+        const float2* wia = tab + R * T + rra * E;
+        const float2* wib = tab + R * T + rrb * E;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float re = 0.f, im = 0.f;
+            if (2 * m < n) re = __ldg(xr + 2 * m);
+            if (2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+            v[i] = cmul(make_float2(re, im), cmul(wt, c2(__ldg(wia + i), __ldg(wib + i))));
+        }
+        FFT::run(v, s, t, a.btw + fft_twiddle_offset(LZ));
+        if (on) {
+            float2* za = ws + (size_t)ra * LZ + t;
+            float2* zb = ws + (size_t)rb * LZ + t;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                za[T * i] = lane_a(v[i]);
+                zb[T * i] = lane_b(v[i]);
+            }
+        }
+        __syncthreads();                                         // s is reused by the next round
+    }
+    // (the barrier above also makes every thread's workspace stores visible)
+    float2* Xr = a.X + it.out_off;
+    const float2* wp = tab + R * T + R * E;                      // w_{2H}^k, k <= H/2
+    const int mask = R - 1;
+#pragma unroll 4
+    for (int k = tid; k <= H / 2; k += kFftQueueThreads) {
+        const int km = (H - k) & (H - 1);
+        const float2 A = ws[(size_t)(k & mask) * LZ + (k >> logR)];
+        const float2 B = ws[(size_t)(km & mask) * LZ + (km >> logR)];
+        unpack_pair(Xr, k, H, A, B, __ldg(wp + k));
+    }
+}
+
+__global__ void __launch_bounds__(kFftQueueThreads, 2) k_fft_queue(FftQueueArgs a) {
+    extern __shared__ float4 smem4[];
+    __shared__ int s_unit;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_unit = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int ui = s_unit;
+        if (ui >= a.nunits) return;
+        const FftUnit u = a.units[ui];
+#define SPEC_QUEUE_CASE(lz)                                                    \
+    case lz:                                                                   \
+        if (u.mode == 0) fft_queue_full<lz>(a, u, smem4);                      \
+        else if (u.mode == 1) fft_queue_pairs<lz>(a, u, smem4);                \
+        else fft_queue_ws<lz>(a, u, smem4);                                    \
+        break;
+        switch (u.LZ) {
+            SPEC_QUEUE_CASE(16) SPEC_QUEUE_CASE(32) SPEC_QUEUE_CASE(64) SPEC_QUEUE_CASE(128)
+            SPEC_QUEUE_CASE(256) SPEC_QUEUE_CASE(512) SPEC_QUEUE_CASE(1024) SPEC_QUEUE_CASE(2048)
+            SPEC_QUEUE_CASE(4096)
+            default: break;
+        }
+#undef SPEC_QUEUE_CASE
+    }
+}
+
+// 4096 packed pairs of C2 values in padded layout, plus slack for the
+// whole-trace staging (F (padded_len(H) + 2) float2 per unit)
+size_t fft_queue_smem() { return (size_t)kFftQueueThreads * 17 * sizeof(float4) + 1024; }
+
+cudaError_t fft_queue_launch(const RaggedItem* items, const FftUnit* units, int nunits, unsigned* counter,
+                             const float* x_pool, const float2* btw, float2* X_pool, float2* ws, int64_t ws_per_cta,
+                             int ctas, cudaStream_t st) {
+    if (nunits == 0) return cudaSuccess;
+    const size_t smem = fft_queue_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_fft_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    FftQueueArgs a = {};
+    a.items = items; a.units = units; a.nunits = nunits; a.counter = counter;
+    a.x = x_pool; a.X = X_pool; a.btw = btw; a.ws = ws; a.ws_per_cta = ws_per_cta;
+    k_fft_queue<<<(unsigned)std::max(1, std::min(ctas, nunits)), kFftQueueThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Pruned complex FFT with a rotated store: Y[(j + shift) mod K] = U[j],
 // U = FFT_K of u[0 .. nin-1] zero-padded to K.  The same residue
 // decomposition as above (R = K/LZ pre-twiddled LZ-point FFTs, a cluster of
@@ -796,6 +1240,18 @@ static FftKernel fft_kernel_fixed_for(int LZ, int R) {
     return nullptr;
 }
 
+// (LZ, R) pairs with a compiled cluster kernel (one trace per cluster of
+// R LZ/8192 CTAs)
+static FftKernel fft_kernel_cluster_for(int LZ, int R) {
+#define SPEC_CLUSTER(lz, r) if (LZ == lz && R == r) return k_fft_real_cluster<lz, r>;
+    SPEC_CLUSTER(4096, 4) SPEC_CLUSTER(4096, 8) SPEC_CLUSTER(4096, 16)
+    SPEC_CLUSTER(2048, 8) SPEC_CLUSTER(2048, 16) SPEC_CLUSTER(2048, 32)
+    SPEC_CLUSTER(1024, 16) SPEC_CLUSTER(1024, 32) SPEC_CLUSTER(1024, 64)
+#undef SPEC_CLUSTER
+    return nullptr;
+}
+constexpr size_t kClusterSmem = (size_t)(pidx8(kClusterRun) + 2) * sizeof(float2);
+
 static FftKernel fft_kernel_for(int LZ, int emax) {
     if (emax == 32) {
         switch (LZ) {
@@ -837,7 +1293,7 @@ int fft_emax_for(int LF) {
     return (forced == 32 && (LF == 512 || LF == 1024 || LF == 8192)) ? 32 : 16;
 }
 
-bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why) {
+bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why, bool allow_cluster) {
     *p = FftPlan();
     if (n_fft == 1) return true;
     const int64_t H = n_fft / 2;
@@ -876,6 +1332,20 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
     p->paired = C > 1 && (p->Rc % 2 == 0 || (p->Rc == 1 && R == 2));
     p->dual = p->Rc >= 2 && LZ >= 16 && LZ <= 4096 && p->emax == 16 && !p->paired && (p->Rc / 2) * T <= 256;
     p->fixed = p->dual && C == 1 && fft_kernel_fixed_for((int)LZ, (int)R) != nullptr;
+    p->clustered = allow_cluster && fft_kernel_cluster_for((int)LZ, (int)R) != nullptr && fft_emax_for((int)LZ) == 16;
+    if (p->clustered) {
+        // one cluster of R LZ/8192 CTAs per trace, 256 threads each
+        p->C = (int)(R * LZ / kClusterRun);
+        p->Rc = (int)(R / p->C);
+        p->paired = p->dual = p->fixed = false;
+        p->E = 16;
+        p->T = (int)LZ / 16;
+        p->F = 1;
+        p->trace_smem = (int)(kClusterSmem / sizeof(float2));
+        p->threads = 256;
+        p->smem = kClusterSmem;
+        return true;
+    }
     const int per_trace = p->dual ? (p->Rc / 2) * T : p->Rc * T;
     p->F = 1;
     if (C == 1) {
@@ -893,6 +1363,7 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 }
 
 int fft_table_entries(const FftPlan& p) {
+    if (p.clustered) return 2 * (cluster_tw4_index(p.H) + fft_twiddle_entries(p.LZ));
     const int generic = p.R * p.T + p.R * p.E + p.H / 2 + 1;
     if (!p.fixed) return generic;
     // + packed pre-twiddles [R/2][LZ] and BlockFFT<LZ> twiddles, float4 each
@@ -906,6 +1377,31 @@ void fft_fill_table(const FftPlan& p, float2* host) {
         const double ang = two_pi * (double)(num % den) / (double)den;
         return make_float2((float)std::cos(ang), (float)-std::sin(ang));
     };
+    auto tw4_fill = [&](float4* t4) {
+        // BlockFFT<LZ> twiddles of the radix-16 layout as packed pairs (c, c, s, s)
+        const int lg = ilog2(p.LZ), npb = lg / 4, rem = 1 << (lg % 4);
+        const int npass = npb + (rem > 1 ? 1 : 0);
+        int ns = 1;
+        for (int q = 0; q < npass; ++q) {
+            const int Rq = q < npb ? 16 : rem;
+            if (q >= 1)
+                for (int r = 1; r < Rq; ++r)
+                    for (int k = 0; k < ns; ++k) {
+                        const float2 e = w((int64_t)r * k, (int64_t)ns * Rq);
+                        t4[ns - 16 + (r - 1) * ns + k] = make_float4(e.x, e.x, e.y, e.y);
+                    }
+            ns *= Rq;
+        }
+    };
+    if (p.clustered) {
+        for (int64_t k = 0; k <= H / 2; ++k) host[k] = w(k, 2 * H);
+        float2* pre = host + cluster_pre_offset(p.H);
+        for (int g = 0; g < p.R / 2; ++g)
+            for (int m = 0; m < p.LZ; ++m)
+                pre[(int64_t)g * p.LZ + m] = w((int64_t)(g == 0 ? p.R / 2 : g) * m, H);
+        tw4_fill(reinterpret_cast<float4*>(host) + cluster_tw4_index(p.H));
+        return;
+    }
     float2* o = host;
     for (int r = 0; r < p.R; ++r)
         for (int t = 0; t < p.T; ++t) *o++ = w((int64_t)r * t, H);
@@ -920,21 +1416,7 @@ void fft_fill_table(const FftPlan& p, float2* host) {
             const float2 wa = w((int64_t)g * m, H), wb = w((int64_t)(g + p.R / 2) * m, H);
             *o4++ = make_float4(wa.x, wb.x, wa.y, wb.y);
         }
-    // BlockFFT<LZ> twiddles of the radix-16 layout as packed pairs (c, c, s, s)
-    const int lg = ilog2(p.LZ), npb = lg / 4, rem = 1 << (lg % 4);
-    const int npass = npb + (rem > 1 ? 1 : 0);
-    float4* t4 = reinterpret_cast<float4*>(host) + fixed_tw4_index(p.LZ, p.R);
-    int ns = 1;
-    for (int q = 0; q < npass; ++q) {
-        const int Rq = q < npb ? 16 : rem;
-        if (q >= 1)
-            for (int r = 1; r < Rq; ++r)
-                for (int k = 0; k < ns; ++k) {
-                    const float2 e = w((int64_t)r * k, (int64_t)ns * Rq);
-                    t4[ns - 16 + (r - 1) * ns + k] = make_float4(e.x, e.x, e.y, e.y);
-                }
-        ns *= Rq;
-    }
+    tw4_fill(reinterpret_cast<float4*>(host) + fixed_tw4_index(p.LZ, p.R));
 }
 
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
@@ -944,6 +1426,28 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
     if (p.H == 0) {   // n_fft == 1
         k_fft_len1<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(x, batch, ld_x, X, ld_X);
         return cudaGetLastError();
+    }
+    if (p.clustered) {
+        FftKernel kc = fft_kernel_cluster_for(p.LZ, p.R);
+        cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmem);
+        if (e != cudaSuccess) return e;
+        FftArgs a = {};
+        a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
+        a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = p.C; a.F = 1;
+        a.tab = tab; a.X = X; a.ld_X = ld_X; a.items = items;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(batch * p.C));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = kClusterSmem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = p.C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kc, a);
     }
     const bool dual = p.dual && lanes != 1;
     if (dual && p.fixed) {

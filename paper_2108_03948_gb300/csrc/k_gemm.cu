@@ -27,6 +27,7 @@
 // context's status word, and the CTA drains its copies and products in
 // flight, frees its tensor memory and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <mutex>
@@ -48,6 +49,9 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 // FP16 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at
 // bits 17-22, M >> 4 at bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// The same with A and B BF16 (format 1 at bits 7-9 and 10-12; both operands
+// always share one format)
+constexpr uint32_t kIdescBf16 = kIdesc | (1u << 7) | (1u << 10);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -115,11 +119,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate,
+                                         uint32_t idesc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -148,7 +153,7 @@ struct GemmArgs {
     int kblocks;               // padded N / 64
     int ntn;                   // column tiles
     int64_t tiles;
-    int terms;                 // 3 (split) or 1
+    int terms;                 // 3 (FP16 split), 1 (one FP16 product) or -1 (one BF16 product)
     const int* row_pow;        // per row: log2 of its scale s
     const int* col_pow;        // per output bin k: log2 of Z's column scale (spiral contours), or null
     float* out;
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     const Guard g{abort_flag, a.status, a.timeout_ns};
     const uint32_t stage_tx = a.terms == 3 ? (uint32_t)STAGE_BYTES : (uint32_t)(TILE_A + TILE_B);
+    const uint32_t idesc = a.terms < 0 ? kIdescBf16 : kIdesc;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -254,12 +260,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint64_t ah = sw128_desc(sa + ks * 32);
                         const uint64_t bh = sw128_desc(sa + 2 * TILE_A + ks * 32);
                         const uint32_t accum = (kb | ks) != 0;
-                        umma_f16(d1, ah, bh, accum);
+                        umma_f16(d1, ah, bh, accum, idesc);
                         if (a.terms == 3) {
                             const uint64_t al = sw128_desc(sa + TILE_A + ks * 32);
                             const uint64_t bl = sw128_desc(sa + 2 * TILE_A + TILE_B + ks * 32);
-                            umma_f16(d2, ah, bl, accum);
-                            umma_f16(d2, al, bh, 1u);
+                            umma_f16(d2, ah, bl, accum, idesc);
+                            umma_f16(d2, al, bh, 1u, idesc);
                         }
                     }
                     any = true;
@@ -348,6 +354,12 @@ __global__ void k_gemm_split_x(const float* x, int64_t batch, int n, int64_t ld_
     __half* lr = xl + row * np;
     for (int i = lane; i < np; i += 32) {
         const float v = i < n ? ldexpf(xr[i], p) : 0.f;
+        if (terms < 0) {
+            // one BF16 part, stored in the same 16-bit slots
+            const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+            hr[i] = __ushort_as_half(__bfloat16_as_ushort(bh));
+            continue;
+        }
         const __half h = __float2half_rn(v);
         hr[i] = h;
         if (terms == 3) lr[i] = __float2half_rn((v - __half2float(h)) * 2048.f);
@@ -356,8 +368,9 @@ __global__ void k_gemm_split_x(const float* x, int64_t batch, int n, int64_t ld_
 }
 
 // Z rows c < 2M (cos for c = 2k, -sin for c = 2k+1) at the exact phase
-// A n + B k n (64-bit fixed point, cycles), scaled by 2^14 and split.
-__global__ void k_gemm_build_z(int m, int n, int np, uint64_t A, uint64_t B, __half* zh, __half* zl) {
+// A n + B k n (64-bit fixed point, cycles), scaled by 2^14 and split (or, for
+// the BF16 form, rounded once to BF16 into zh; zl then holds zeros).
+__global__ void k_gemm_build_z(int m, int n, int np, uint64_t A, uint64_t B, __half* zh, __half* zl, int bf16) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)2 * m * np) return;
     const int c = (int)(idx / np);
@@ -372,6 +385,11 @@ __global__ void k_gemm_build_z(int m, int n, int np, uint64_t A, uint64_t B, __h
         v = (c & 1) ? -s : co;
     }
     v *= 16384.0;
+    if (bf16) {
+        zh[idx] = __ushort_as_half(__bfloat16_as_ushort(__double2bfloat16(v)));
+        zl[idx] = __float2half_rn(0.f);
+        return;
+    }
     const __half h = __float2half_rn((float)v);
     zh[idx] = h;
     zl[idx] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
@@ -446,12 +464,12 @@ size_t gemm_work_bytes(int64_t batch, int64_t n) {
     return ((size_t)2 * batch * np * sizeof(__half) + 255) / 256 * 256 + (size_t)batch * sizeof(int);
 }
 
-cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, cudaStream_t st) {
+cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, cudaStream_t st, bool bf16) {
     const int np = gemm_padded_n(n);
     __half* zh = (__half*)z;
     __half* zl = zh + (size_t)2 * m * np;
     const int64_t total = (int64_t)2 * m * np;
-    k_gemm_build_z<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((int)m, (int)n, np, A, B, zh, zl);
+    k_gemm_build_z<<<(unsigned)((total + 255) / 256), 256, 0, st>>>((int)m, (int)n, np, A, B, zh, zl, bf16 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -522,4 +522,119 @@ cudaError_t zoom_fir_ragged_launch(const RaggedItem* items, int64_t count, int c
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Ragged batches as one persistent launch (work queue): every trace has its
+// own N, D, taps and K = N_FFT/D <= 16384.  A unit holds up to 16384/K traces
+// of one K on a 1024-thread CTA, each trace on K/16 threads with its own
+// slice of shared memory (taps, polyphase trace, FFT area: the k_zoom
+// layout).  Where the slices of 16384/K traces do not fit, the unit holds F
+// fewer traces and the remaining thread groups run the FFT's barriers on a
+// scratch FFT area, touching nothing else.  Units (largest K first) are
+// popped from an atomic counter by persistent CTAs, one per SM.
+struct ZoomQueueArgs {
+    const RaggedItem* items;
+    const ZoomUnit* units;
+    int nunits;
+    unsigned* counter;
+    const float* x;
+    const float* taps;
+    float2* X;
+    const float2* tw;          // BlockFFT twiddles of every size (radix-16 layout)
+};
+
+constexpr int kZoomQueueThreads = 1024;
+
+template <int K>
+__device__ __forceinline__ void zoom_queue_unit(const ZoomQueueArgs& a, const ZoomUnit& u, unsigned char* smem) {
+    using FFT = BlockFFT<K, false>;
+    constexpr int E = FFT::E, T = FFT::T;
+    const int f = threadIdx.x / T;
+    const int t = threadIdx.x - f * T;
+    const bool live = f < u.count;                     // u.count <= u.F
+    const RaggedItem it = a.items[u.first + (live ? f : 0)];
+    const int n = it.n, n_taps = it.n_taps, D = it.d, lout = it.lout, rs = it.rs;
+    const int logd = is_pow2_dev(D) ? ilog2c(D) : -1;
+    const uint64_t Cn = it.A;
+    const int J = n_taps - 1;
+    float4* slice = reinterpret_cast<float4*>(smem + (size_t)(f < u.F ? f : 0) * u.slice);
+    float4* tap = slice;
+    float* xs = reinterpret_cast<float*>(slice + n_taps);
+    float2* s = live ? reinterpret_cast<float2*>(slice + n_taps) + (D * rs + 1) / 2
+                     : reinterpret_cast<float2*>(smem + u.scratch);
+    if (live) {
+        const float* taps = a.taps + it.tab_off;
+        for (int k = t; k < n_taps; k += T) {
+            const float h = __ldg(taps + k);
+            const float2 e = unit_fixed(Cn * (uint64_t)k, false);
+            const int q = J - k;
+            tap[k] = make_float4(h * e.x, h * e.y, __int_as_float((q % D) * rs + q / D), 0.f);
+        }
+        const float* xr = a.x + it.x_off;
+        const int total = D * rs;
+        for (int j = t; j < total; j += T) {
+            const int src = j - J;
+            const float xv = (src >= 0 && src < n) ? __ldg(xr + src) : 0.f;
+            const int slot = logd >= 0 ? (j & (D - 1)) * rs + (j >> logd) : (j % D) * rs + j / D;
+            xs[slot] = xv;
+        }
+    }
+    __syncthreads();
+    if (live) zoom_fir_blocked<3, T>(tap, xs, s, n_taps, lout, rs, Cn, D, t);
+    __syncthreads();
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int m = t + T * i;
+        v[i] = (live && m < lout) ? s[pidx(m)] : make_float2(0.f, 0.f);
+    }
+    FFT::run(v, s, t, a.tw + (K <= 16 ? 0 : fft_twiddle_offset(K)));
+    if (!live) return;
+    float2* Xr = a.X + it.out_off;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int j = t + T * i;
+        Xr[(j + K / 2) & (K - 1)] = v[i];
+    }
+}
+
+__global__ void __launch_bounds__(kZoomQueueThreads, 1) k_zoom_queue(ZoomQueueArgs a) {
+    extern __shared__ float4 smem4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
+    __shared__ int s_unit;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_unit = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int ui = s_unit;
+        if (ui >= a.nunits) return;
+        const ZoomUnit u = a.units[ui];
+        switch (u.K) {
+            case 64: zoom_queue_unit<64>(a, u, smem); break;
+            case 128: zoom_queue_unit<128>(a, u, smem); break;
+            case 256: zoom_queue_unit<256>(a, u, smem); break;
+            case 512: zoom_queue_unit<512>(a, u, smem); break;
+            case 1024: zoom_queue_unit<1024>(a, u, smem); break;
+            case 2048: zoom_queue_unit<2048>(a, u, smem); break;
+            case 4096: zoom_queue_unit<4096>(a, u, smem); break;
+            case 8192: zoom_queue_unit<8192>(a, u, smem); break;
+            default: zoom_queue_unit<16384>(a, u, smem); break;
+        }
+    }
+}
+
+int zoom_queue_groups(int K) { return kZoomQueueThreads / (K / 16); }
+
+cudaError_t zoom_queue_launch(const RaggedItem* items, const ZoomUnit* units, int nunits, unsigned* counter,
+                              size_t smem, const float* x_pool, const float* taps_pool, const float2* tw,
+                              float2* X_pool, int ctas, cudaStream_t st) {
+    if (nunits == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_zoom_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ZoomQueueArgs a = {};
+    a.items = items; a.units = units; a.nunits = nunits; a.counter = counter;
+    a.x = x_pool; a.taps = taps_pool; a.X = X_pool; a.tw = tw;
+    k_zoom_queue<<<(unsigned)std::max(1, std::min(ctas, nunits)), kZoomQueueThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace spec

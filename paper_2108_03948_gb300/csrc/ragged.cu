@@ -5,17 +5,20 @@
 // the context:
 //   * every descriptor is validated exactly as the single-shape entry point
 //     would validate it (Section 2.1-2.3 conventions, include/spec.h);
-//   * traces are grouped into classes by kernel instantiation (FFT: residue
-//     length and H; CZT: Bluestein length L; Zoom: K, or (K, pruned length)
-//     for the large path), and a device array of per-trace placements and
-//     parameters (RaggedItem) is uploaded;
-//   * CZT traces get their own chirp tables and kernel spectrum (float64
-//     phases), built once on the device;
-//   * an autotuner times the kernel variants a class admits (FFT: one or two
-//     residues per thread, radix 16 or 32 passes) on the class's own traces
-//     and keeps the fastest;
-//   * one CUDA graph is captured with one launch per class, the classes on
-//     parallel branches, so the whole batch is one graph launch.
+//   * each transform kind runs as one persistent launch over a work queue: a
+//     device array of units (a few traces of one shape, or a part of one long
+//     trace), sorted largest first and popped from an atomic counter by one
+//     CTA per SM (FFT: k_fft_queue; chirp-z: k_czt_queue, with the chirps
+//     evaluated in the kernel and one FFT(v)/L table per distinct (N, M,
+//     band); Zoom: k_zoom_queue);
+//   * traces outside a queue's sizes (FFT residue FFTs above 4096 points,
+//     Zoom K above 16384) are grouped into classes of one kernel shape and
+//     launched as before, on parallel branches of the same graph;
+//   * the autotuner times the alternatives a plan admits (FFT queue: long
+//     traces through a per-CTA workspace or as residue-pair units; FFT
+//     classes: lanes, pass radix, cluster kernel) and keeps the fastest;
+//   * one CUDA graph is captured (counter reset, queue launch, class
+//     branches), so the whole batch is one graph launch.
 // Later calls with the same descriptors replay the graph (re-captured if the
 // pool pointers change).
 #include <cuda_runtime.h>
@@ -24,6 +27,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <set>
 #include <tuple>
 #include <vector>
 
@@ -39,6 +43,7 @@ struct RaggedClass {
     int K = 0, L = 0;
     FftPlan fp;          // FFT (path 0) or pruned complex FFT (path 3)
     int lanes = 1;
+    bool in_queue = false;   // the work queue covers these traces too
     size_t smem = 0;     // Zoom one-CTA: the largest need in the class
     int64_t first = 0, count = 0;
     const float2* tab = nullptr;
@@ -56,6 +61,19 @@ struct RaggedPlan {
     size_t fir_smem = 0;
     float2* tables = nullptr;
     float2* work = nullptr;
+    // work queue (chirp-z: CztUnit; FFT: FftUnit), its length, the counter;
+    // chirp-z: `tables` holds the FFT(v)/L pool
+    void* units = nullptr;
+    int nunits = 0;
+    size_t qsmem = 0;          // Zoom queue: dynamic shared memory of the launch
+    bool use_queue = false;    // the captured graph runs the queue (else the per-shape classes)
+    float t_queue_us = 0.f, t_classes_us = 0.f;   // the two forms as timed when the plan was built
+    float2* vpool = nullptr;   // chirp-z queue: FFT(v)/L per distinct (N, M, band)
+    float2* qws = nullptr;     // FFT queue: per-CTA workspaces (mode 2 units)
+    int64_t qws_per = 0;
+    void* units_alt = nullptr; // FFT queue: the same work as residue-pair units (timed against `units`)
+    int nunits_alt = 0;
+    unsigned* counter = nullptr;
     cudaStream_t cap = nullptr;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> ev;
@@ -74,6 +92,11 @@ void ragged_plan_free(RaggedPlan* p) {
     if (p->items) cudaFree(p->items);
     if (p->tables) cudaFree(p->tables);
     if (p->work) cudaFree(p->work);
+    if (p->units) cudaFree(p->units);
+    if (p->units_alt) cudaFree(p->units_alt);
+    if (p->qws) cudaFree(p->qws);
+    if (p->vpool) cudaFree(p->vpool);
+    if (p->counter) cudaFree(p->counter);
     delete p;
 }
 
@@ -85,6 +108,8 @@ bool same_descs(const RaggedPlan* p, int kind, double fs, const spec_desc* d, in
 }
 
 const float2* tw_for(spec_ctx* c, int LF, int emax = 16) { return c->block_tw + block_twiddle_offset(LF, emax); }
+
+constexpr int kQueueThreads = 256;    // threads of the persistent FFT kernel's CTA (two per SM)
 
 cudaError_t launch_class(spec_ctx* c, RaggedPlan* P, const RaggedClass& k, cudaStream_t s, const float* x,
                          const float* taps, float2* X) {
@@ -146,11 +171,25 @@ spec_status capture(spec_ctx* c, RaggedPlan* P, const float* x, const float* tap
     cudaError_t e = cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return ctx_cuda_fail(c, e, "graph capture");
     cudaError_t le = cudaEventRecord(P->ev[0], P->cap);
+    if (P->use_queue && P->nunits > 0 && le == cudaSuccess) {
+        // one persistent launch over the unit queue
+        le = cudaMemsetAsync(P->counter, 0, sizeof(unsigned), P->cap);
+        if (le == cudaSuccess && P->kind == SPEC_KIND_CZT)
+            le = czt_queue_launch(P->items, (const CztUnit*)P->units, P->nunits, P->counter, x, P->vpool,
+                                  c->block_tw, c->block_tw + block_twiddle_offset(64, 32) - fft_twiddle_offset(64, 32),
+                                  X, c->sms, P->cap);
+        if (le == cudaSuccess && P->kind == SPEC_KIND_ZOOM)
+            le = zoom_queue_launch(P->items, (const ZoomUnit*)P->units, P->nunits, P->counter, P->qsmem, x, taps,
+                                   c->block_tw, X, c->sms, P->cap);
+        if (le == cudaSuccess && P->kind == SPEC_KIND_FFT)
+            le = fft_queue_launch(P->items, (const FftUnit*)P->units, P->nunits, P->counter, x, c->block_tw, X,
+                                  P->qws, P->qws_per, 2 * std::max(1, c->sms), P->cap);
+    }
     size_t br = 0;
     // one branch per class of paths 0-2; the large Zoom path (FIR, then its
     // pruned-FFT classes) forms one more branch
     for (const RaggedClass& k : P->classes) {
-        if (k.path == 3 || le != cudaSuccess) continue;
+        if (k.path == 3 || le != cudaSuccess || (P->use_queue && k.in_queue)) continue;
         cudaStream_t s = P->side[br];
         le = cudaStreamWaitEvent(s, P->ev[0], 0);
         if (le == cudaSuccess) le = launch_class(c, P, k, s, x, taps, X);
@@ -260,7 +299,126 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
     // ---- items, per class, large-zoom classes last ---------------------------
     std::vector<RaggedItem> items;
     items.reserve((size_t)count);
-    int64_t tab_total = 0, work_total = 0;
+    int64_t tab_total = 0, work_total = 0, vp_total = 0;
+    // shapes the work queue covers; their classes are built too, and the plan
+    // keeps whichever of the two graphs (queue or per-shape launches) is faster
+    std::set<std::tuple<int, int, int>> queued;
+    std::vector<CztUnit> units;
+    std::map<int, std::vector<RaggedItem>> vkeys;      // per L: one item per distinct (N, M, B)
+    std::vector<FftUnit> funits, funits_pairs;
+    int64_t ws_per = 0;
+    std::vector<ZoomUnit> zunits;
+    size_t zsmem = 0;
+    if (kind == SPEC_KIND_ZOOM) {
+        // work queue for the one-CTA Zoom classes K in [64, 16384]: units of
+        // traces of one K, as many as their shared-memory slices allow
+        const size_t budget = 227 * 1024 - 1024;
+        for (auto g = groups.rbegin(); g != groups.rend();) {
+            const int path = std::get<0>(g->first), K = std::get<1>(g->first);
+            if (path != 2 || K < 64 || K > 16384) {
+                ++g;
+                continue;
+            }
+            std::vector<Tmp>& tr = g->second;
+            auto need = [&](const Tmp& x) {
+                return (zoom_smem_for(x.it.n_taps, x.it.d, x.it.rs, K) + 15) & ~(size_t)15;
+            };
+            std::stable_sort(tr.begin(), tr.end(), [&](const Tmp& p1, const Tmp& p2) { return need(p1) > need(p2); });
+            const int G = zoom_queue_groups(K);
+            const size_t scratch = ((size_t)padded_len(K) * sizeof(float2) + 15) & ~(size_t)15;
+            size_t j = 0;
+            while (j < tr.size()) {
+                const size_t slice = need(tr[j]);                  // largest need of the unit (sorted)
+                int F = (int)std::min<size_t>((size_t)G, budget / slice);
+                if (F < G || tr.size() - j < (size_t)G) {
+                    // some groups idle: keep room for the scratch FFT area
+                    F = (int)std::min<size_t>((size_t)F, (budget - scratch) / slice);
+                }
+                if (F < 1) return bail(ctx_fail(c, SPEC_EUNSUPPORTED, "zoom: a trace exceeds the queue's shared memory"));
+                const int cnt = (int)std::min<size_t>((size_t)F, tr.size() - j);
+                ZoomUnit zu{K, (int)items.size(), cnt, F, (int)slice, (int)(F * slice)};
+                zsmem = std::max(zsmem, cnt < G ? F * slice + scratch : F * slice);
+                zunits.push_back(zu);
+                for (int q = 0; q < cnt; ++q) items.push_back(tr[j + q].it);
+                j += cnt;
+            }
+            queued.insert(g->first);
+            ++g;
+        }
+    }
+    if (kind == SPEC_KIND_FFT) {
+        // work queue for every (H, LZ) the persistent kernel handles: whole
+        // traces per unit up to H = 16384, residue pairs of one trace above;
+        // largest LZ (then H) first, a trace's units adjacent
+        for (auto g = groups.rbegin(); g != groups.rend();) {
+            const int H = std::get<1>(g->first), LZ = std::get<2>(g->first);
+            const int R = H / LZ;
+            FftPlan fp;
+            std::string why;
+            const bool ok = LZ >= 16 && LZ <= 4096 && R >= 2 && H >= 32 &&
+                            fft_plan(1, 2 * (int64_t)LZ, 2 * (int64_t)H, &fp, &why) && fp.emax == 16 && fp.E == 16;
+            if (!ok) {
+                ++g;
+                continue;
+            }
+            const float2* tab = nullptr;
+            spec_status ts = ctx_plan_table(c, 0, fp, &tab);
+            if (ts != SPEC_OK) return bail(ts);
+            const int T = LZ / 16;
+            if ((R / 2) * T <= kQueueThreads) {
+                const int F = kQueueThreads / ((R / 2) * T);
+                for (size_t j = 0; j < g->second.size(); ++j) {
+                    if (j % F == 0) {
+                        funits.push_back(FftUnit{tab, LZ, ilog2(R), (int)items.size(), 0, 0, 0});
+                        funits_pairs.push_back(funits.back());
+                    }
+                    ++funits.back().count;
+                    ++funits_pairs.back().count;
+                    items.push_back(g->second[j].it);
+                }
+            } else {
+                // one trace per unit through the CTA's workspace (mode 2); the
+                // alternative list splits it into residue-pair units (mode 1)
+                const int G = kQueueThreads / T;
+                for (Tmp& tr : g->second) {
+                    funits.push_back(FftUnit{tab, LZ, ilog2(R), (int)items.size(), 1, 0, 2});
+                    for (int g0 = 0; g0 < R / 2; g0 += G)
+                        funits_pairs.push_back(
+                            FftUnit{tab, LZ, ilog2(R), (int)items.size(), std::min(G, R / 2 - g0), g0, 1});
+                    items.push_back(tr.it);
+                }
+                ws_per = std::max<int64_t>(ws_per, H);
+            }
+            queued.insert(g->first);
+            ++g;
+        }
+    }
+    if (kind == SPEC_KIND_CZT) {
+        // work queue: units of 16384/L traces, largest L first; FFT(v)/L
+        // shared by every trace with the same (N, M, B)
+        std::map<std::tuple<int, int, uint64_t>, int64_t> voff;
+        for (auto g = groups.rbegin(); g != groups.rend(); ++g) {
+            const int L = std::get<1>(g->first);
+            const int per = czt_queue_unit_traces(L);
+            for (size_t j = 0; j < g->second.size(); ++j) {
+                RaggedItem it = g->second[j].it;
+                const auto key = std::make_tuple(it.n, it.m, it.B);
+                auto f = voff.find(key);
+                if (f == voff.end()) {
+                    f = voff.emplace(key, vp_total).first;
+                    RaggedItem kk = it;
+                    kk.tab_off = vp_total;
+                    vkeys[L].push_back(kk);
+                    vp_total += L;
+                }
+                it.tab_off = f->second;
+                if (j % per == 0) units.push_back(CztUnit{L, (int)items.size(), 0, 0});
+                ++units.back().count;
+                items.push_back(it);
+            }
+        }
+        for (auto& kv : groups) queued.insert(kv.first);
+    }
     for (auto& kv : groups) {
         const int path = std::get<0>(kv.first);
         RaggedClass k;
@@ -295,6 +453,7 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
             }
             items.push_back(t.it);
         }
+        k.in_queue = queued.count(kv.first) > 0;
         P->classes.push_back(k);
     }
     for (const RaggedClass& k : P->classes)
@@ -307,7 +466,52 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
     if (e == cudaSuccess && !items.empty())
         e = cudaMemcpy(P->items, items.data(), items.size() * sizeof(RaggedItem), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && tab_total > 0) e = cudaMalloc(&P->tables, (size_t)tab_total * sizeof(float2));
+    if (e == cudaSuccess && vp_total > 0) e = cudaMalloc(&P->vpool, (size_t)vp_total * sizeof(float2));
     if (e == cudaSuccess && work_total > 0) e = cudaMalloc(&P->work, (size_t)work_total * sizeof(float2));
+    if (e == cudaSuccess && !zunits.empty()) {
+        P->nunits = (int)zunits.size();
+        P->qsmem = zsmem;
+        e = cudaMalloc(&P->units, zunits.size() * sizeof(ZoomUnit));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->units, zunits.data(), zunits.size() * sizeof(ZoomUnit), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&P->counter, sizeof(unsigned));
+    }
+    if (e == cudaSuccess && !funits.empty()) {
+        P->nunits = (int)funits.size();
+        e = cudaMalloc(&P->units, funits.size() * sizeof(FftUnit));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->units, funits.data(), funits.size() * sizeof(FftUnit), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&P->counter, sizeof(unsigned));
+        if (e == cudaSuccess && ws_per > 0) {
+            P->qws_per = ws_per;
+            e = cudaMalloc(&P->qws, (size_t)(2 * std::max(1, c->sms)) * (size_t)ws_per * sizeof(float2));
+        }
+        if (e == cudaSuccess && funits_pairs.size() != funits.size()) {
+            P->nunits_alt = (int)funits_pairs.size();
+            e = cudaMalloc(&P->units_alt, funits_pairs.size() * sizeof(FftUnit));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(P->units_alt, funits_pairs.data(), funits_pairs.size() * sizeof(FftUnit),
+                               cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess && !units.empty()) {
+        P->nunits = (int)units.size();
+        e = cudaMalloc(&P->units, units.size() * sizeof(CztUnit));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->units, units.data(), units.size() * sizeof(CztUnit), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&P->counter, sizeof(unsigned));
+        for (auto& kv : vkeys) {
+            if (e != cudaSuccess) break;
+            RaggedItem* dk = nullptr;
+            e = cudaMalloc(&dk, kv.second.size() * sizeof(RaggedItem));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(dk, kv.second.data(), kv.second.size() * sizeof(RaggedItem), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = czt_vpool_build(kv.first, dk, (int64_t)kv.second.size(), P->vpool, c->block_tw, P->cap);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(P->cap);
+            if (dk) cudaFree(dk);
+        }
+    }
     if (e != cudaSuccess) return bail(ctx_cuda_fail(c, e, "ragged plan"));
     // ---- per-class tables ------------------------------------------------------
     for (RaggedClass& k : P->classes) {
@@ -322,22 +526,71 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
     }
     e = cudaStreamSynchronize(P->cap);
     if (e != cudaSuccess) return bail(ctx_cuda_fail(c, e, "ragged plan"));
+    // ---- autotune: the FFT queue's long traces as whole-trace workspace units
+    //      or as residue-pair units, by timing the launch both ways -----------
+    if (P->units_alt) {
+        auto time_queue = [&](void* u, int nu) {
+            cudaEvent_t ea, eb;
+            cudaEventCreate(&ea);
+            cudaEventCreate(&eb);
+            float best = 1e30f;
+            for (int r = 0; r < 4; ++r) {
+                cudaEventRecord(ea, P->cap);
+                cudaError_t le = cudaMemsetAsync(P->counter, 0, sizeof(unsigned), P->cap);
+                if (le == cudaSuccess)
+                    le = fft_queue_launch(P->items, (const FftUnit*)u, nu, P->counter, x, c->block_tw, X, P->qws,
+                                          P->qws_per, 2 * std::max(1, c->sms), P->cap);
+                cudaEventRecord(eb, P->cap);
+                if (le != cudaSuccess || cudaEventSynchronize(eb) != cudaSuccess) {
+                    best = 1e30f;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ea, eb);
+                if (r > 0) best = std::min(best, ms);
+            }
+            cudaEventDestroy(ea);
+            cudaEventDestroy(eb);
+            cudaGetLastError();
+            return best;
+        };
+        const float t_ws = time_queue(P->units, P->nunits);
+        const float t_pairs = time_queue(P->units_alt, P->nunits_alt);
+        if (t_pairs < t_ws) {
+            std::swap(P->units, P->units_alt);
+            std::swap(P->nunits, P->nunits_alt);
+        }
+    }
     // ---- autotune: FFT classes choose lanes and pass radix by timing ----------
     for (RaggedClass& k : P->classes) {
         if (k.path != 0) continue;
         RaggedClass best = k;
         best.tuned_us = 1e30f;
+        RaggedClass base = k;
+        {
+            // the cluster kernel (where it has an instance) is one more candidate
+            RaggedClass cl = k;
+            std::string why;
+            if (fft_plan(k.count, 2 * (int64_t)k.fp.LZ, 2 * (int64_t)k.fp.H, &cl.fp, &why, true) && cl.fp.clustered &&
+                ctx_plan_table(c, 0, cl.fp, &cl.tab) == SPEC_OK) {
+                const float t = 1e3f * time_class(c, P, cl, x, taps, X);
+                if (t < best.tuned_us) {
+                    best = cl;
+                    best.tuned_us = t;
+                }
+            }
+        }
         for (int emax : {16, 32}) {
             if (emax == 32 && !(k.fp.LZ == 512 || k.fp.LZ == 1024 || k.fp.LZ == 8192)) continue;
             for (int lanes : {1, 2}) {
-                RaggedClass cand = k;
+                RaggedClass cand = base;
                 cand.fp.emax = emax;
                 cand.fp.E = std::min(emax, cand.fp.LZ);
                 cand.fp.T = cand.fp.LZ / cand.fp.E;
                 if (emax == 32) cand.fp.dual = cand.fp.fixed = false;
                 if (lanes == 2 && !cand.fp.dual) continue;
                 cand.lanes = lanes;
-                if (emax != k.fp.emax && ctx_plan_table(c, 0, cand.fp, &cand.tab) != SPEC_OK) continue;
+                if (emax != base.fp.emax && ctx_plan_table(c, 0, cand.fp, &cand.tab) != SPEC_OK) continue;
                 const float t = 1e3f * time_class(c, P, cand, x, taps, X);
                 if (t < best.tuned_us) {
                     best = cand;
@@ -346,6 +599,44 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
             }
         }
         if (best.tuned_us < 1e29f) k = best;
+    }
+    // ---- autotune: the work queue against the per-shape launches -------------
+    P->use_queue = P->nunits > 0;
+    if (P->nunits > 0) {
+        auto time_graph = [&]() {
+            if (capture(c, P, x, taps, X) != SPEC_OK) return 1e30f;
+            cudaEvent_t ea, eb;
+            cudaEventCreate(&ea);
+            cudaEventCreate(&eb);
+            float best = 1e30f;
+            for (int r = 0; r < 4; ++r) {
+                cudaEventRecord(ea, P->cap);
+                cudaError_t le = cudaGraphLaunch(P->exec, P->cap);
+                cudaEventRecord(eb, P->cap);
+                if (le != cudaSuccess || cudaEventSynchronize(eb) != cudaSuccess) {
+                    best = 1e30f;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ea, eb);
+                if (r > 0) best = std::min(best, ms);
+            }
+            cudaEventDestroy(ea);
+            cudaEventDestroy(eb);
+            cudaGetLastError();
+            return best;
+        };
+        P->use_queue = false;
+        const float t_classes = time_graph();
+        P->use_queue = true;
+        const float t_queue = time_graph();
+        P->use_queue = c->ragged_queue >= 0 ? c->ragged_queue == 1 : t_queue <= t_classes;
+        P->t_queue_us = 1e3f * t_queue;
+        P->t_classes_us = 1e3f * t_classes;
+        if (P->exec) {
+            cudaGraphExecDestroy(P->exec);      // captured again for the chosen form by the caller
+            P->exec = nullptr;
+        }
     }
     *out = P;
     return SPEC_OK;
@@ -404,12 +695,35 @@ extern "C" spec_status spec_ragged(spec_ctx* c, int kind, const spec_desc* descs
 }
 
 // Kernel launches in one replay of the cached plan for these descriptors
-// (one per class, plus the FIR launch of the large Zoom path); -1 if the
-// context holds no such plan.
+// (the queue launch, one per remaining class, plus the FIR launch of the
+// large Zoom path); -1 if the context holds no such plan.
 extern "C" int64_t spec_ragged_launches(const spec_ctx* c, int kind, const spec_desc* descs, int64_t count,
                                         double fs) {
     if (!c || count < 0 || (count > 0 && !descs)) return -1;
     for (const RaggedPlan* p : c->ragged)
-        if (same_descs(p, kind, fs, descs, count)) return (int64_t)p->classes.size() + (p->fir_count > 0 ? 1 : 0);
+        if (same_descs(p, kind, fs, descs, count)) {
+            int64_t n = (p->fir_count > 0 ? 1 : 0) + (p->use_queue ? 1 : 0);
+            for (const RaggedClass& k : p->classes)
+                if (k.path != 3 && !(p->use_queue && k.in_queue)) ++n;
+            for (const RaggedClass& k : p->classes)
+                if (k.path == 3) ++n;
+            return n;
+        }
+    return -1;
+}
+
+// How the cached plan for these descriptors runs: 1 if its graph launches the
+// persistent work queue (0: the per-shape launches), and the two forms' times
+// measured when the plan was built (microseconds; 0 where there was no queue).
+// -1 if the context holds no such plan.
+extern "C" int spec_ragged_plan_info(const spec_ctx* c, int kind, const spec_desc* descs, int64_t count, double fs,
+                                     float* t_queue_us, float* t_classes_us) {
+    if (!c || count < 0 || (count > 0 && !descs)) return -1;
+    for (const RaggedPlan* p : c->ragged)
+        if (same_descs(p, kind, fs, descs, count)) {
+            if (t_queue_us) *t_queue_us = p->t_queue_us;
+            if (t_classes_us) *t_classes_us = p->t_classes_us;
+            return p->use_queue ? 1 : 0;
+        }
     return -1;
 }

@@ -251,7 +251,7 @@ spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, 
 // complex FFT (kind 1), built on the host in float64 and cached.
 spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab) {
     for (auto& it : c->fft)
-        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax && it.fixed == (kind == 0 && p.fixed)) {
+        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax && it.layout == (kind != 0 ? 0 : p.clustered ? 2 : p.fixed ? 1 : 0)) {
             *tab = it.tab;
             return SPEC_OK;
         }
@@ -260,7 +260,7 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     ne.H = p.H;
     ne.LZ = p.LZ;
     ne.emax = p.emax;
-    ne.fixed = kind == 0 && p.fixed;
+    ne.layout = kind != 0 ? 0 : p.clustered ? 2 : p.fixed ? 1 : 0;
     std::vector<float2> host((size_t)(kind == 0 ? fft_table_entries(p) : c2c_table_entries(p)));
     if (kind == 0) fft_fill_table(p, host.data());
     else c2c_fill_table(p, host.data());
@@ -273,21 +273,6 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     c->fft.push_back(ne);
     *tab = ne.tab;
     return SPEC_OK;
-}
-
-// SPEC_CZT_AUTO: the split-FP16 GEMM when its modelled time per trace is
-// clearly below Bluestein's and the batch fills the GPU with tiles.  Model
-// (measured on GB300): GEMM 12 N M flop at 1.4 PFLOP/s plus 8 N bytes of
-// split traffic at 6 TB/s; Bluestein 0.39 ps x L log2 L (560 us for 65536
-// traces at L = 2048, 80 us for 4096 at L = 4096).
-bool auto_prefers_gemm(const spec_ctx* c, int64_t batch, int64_t n, int64_t m) {
-    if (gemm_z_bytes(n, m) > (size_t(1) << 31)) return false;
-    const int64_t tiles = (batch + 127) / 128 * ((2 * m + 127) / 128);
-    if (tiles < std::max(1, c->sms)) return false;
-    const double L = (double)next_pow2(std::max<int64_t>(16, n + m - 1));
-    const double t_gemm = 12.0 * (double)n * (double)m / 1.4e15 + 8.0 * (double)n / 6e12;
-    const double t_blue = 0.39e-12 * L * std::log2(L);
-    return t_gemm < 0.9 * t_blue;
 }
 
 // Chirp-z as the tensor-core product x Z^T (k_gemm.cu): Z cached per
@@ -318,8 +303,9 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     const uint64_t A = cycles_to_fixed(f1 / fs);
     const uint64_t B = cycles_to_fixed(step / fs);
     GemmZEntry* en = nullptr;
+    const bool bf16 = terms < 0;
     for (auto& it : c->gemm_z)
-        if (it.n == n && it.m == m && it.A == A && it.B == B && it.a0 == a0 && it.w0 == w0) en = &it;
+        if (it.n == n && it.m == m && it.A == A && it.B == B && it.a0 == a0 && it.w0 == w0 && it.bf16 == bf16) en = &it;
     if (!en) {
         if (c->gemm_z.size() >= kCztCacheMax) {
             auto lru = std::min_element(c->gemm_z.begin(), c->gemm_z.end(),
@@ -330,7 +316,7 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
             c->gemm_z.erase(lru);
         }
         GemmZEntry ne;
-        ne.n = n; ne.m = m; ne.A = A; ne.B = B; ne.a0 = a0; ne.w0 = w0;
+        ne.n = n; ne.m = m; ne.A = A; ne.B = B; ne.a0 = a0; ne.w0 = w0; ne.bf16 = bf16;
         const size_t zb = (gemm_z_bytes(n, m) + 255) / 256 * 256;
         cudaError_t e = cudaMalloc(&ne.z, zb + (spiral ? (size_t)m * sizeof(int) : 0));
         if (e != cudaSuccess) return cuda_fail(c, e, "GEMM Z table");
@@ -342,7 +328,7 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         }
         if (e == cudaSuccess)
             e = spiral ? gemm_build_z_spiral(n, m, A, B, std::log(a0), std::log(w0), ne.col_pow, ne.z, st)
-                       : gemm_build_z(n, m, A, B, ne.z, st);
+                       : gemm_build_z(n, m, A, B, ne.z, st, bf16);
         if (e == cudaSuccess) e = cudaEventRecord(ne.ready, st);
         if (e != cudaSuccess) {
             cudaFree(ne.z);
@@ -457,6 +443,13 @@ spec_status spec_ctx_create(spec_ctx** ctx, int device) {
     }
     c->device = device;
     if (const char* ev = std::getenv("SPEC_LANES")) c->lanes = std::atoi(ev);
+    if (const char* ev = std::getenv("SPEC_FFT_CLUSTER")) c->fft_cluster = std::atoi(ev) == 1;
+    if (const char* ev = std::getenv("SPEC_RAGGED_QUEUE")) c->ragged_queue = std::atoi(ev) == 1 ? 1 : 0;
+    c->tune_device = device_tag(device);
+    if (const char* ev = std::getenv("SPEC_AUTOTUNE_CACHE")) {
+        c->tune_path = ev;
+        if (!c->tune_path.empty()) tune_file_read(c->tune_path, c->tune_device, &c->tune);
+    }
     {
         std::vector<float2> host((size_t)block_twiddle_total());
         block_twiddle_fill(host.data());
@@ -567,7 +560,7 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     FftPlan p;
     LongPlan lp;
     std::string why, why_long;
-    const bool one_pass = fft_plan(batch, n, n_fft, &p, &why);
+    const bool one_pass = fft_plan(batch, n, n_fft, &p, &why, c->fft_cluster);
     if (!one_pass && !long_fft_plan(n, n_fft, &lp, &why_long))
         return fail(c, SPEC_EUNSUPPORTED, why + "; " + why_long);
     if (batch == 0) return SPEC_OK;
@@ -604,12 +597,20 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     spec_status s = check_common(c, x, batch, n, ld_x, fs, X, m, ld_X);
     if (s != SPEC_OK) return s;
     if (!is_finite(f1) || !is_finite(f2)) return fail(c, SPEC_EINVAL, "f1 and f2 must be finite");
-    if (mode < SPEC_CZT_AUTO || mode > SPEC_CZT_GEMM_F16X1) return fail(c, SPEC_EINVAL, "unknown CZT mode");
+    if (mode < SPEC_CZT_AUTO || mode > SPEC_CZT_GEMM_BF16X1) return fail(c, SPEC_EINVAL, "unknown CZT mode");
     // AUTO is decided on the whole batch (chunks of a host-buffer call then
     // all run the same arithmetic)
-    if (mode == SPEC_CZT_AUTO)
-        mode = auto_prefers_gemm(c, batch, n, m) ? SPEC_CZT_GEMM_F16X3 : SPEC_CZT_BLUESTEIN;
-    const bool gemm = mode == SPEC_CZT_GEMM_F16X3 || mode == SPEC_CZT_GEMM_F16X1;
+    if (mode == SPEC_CZT_AUTO) {
+        // measured on a probe batch the first time (n, m, batch size) is
+        // seen, then remembered (autotune.cu)
+        mode = SPEC_CZT_BLUESTEIN;
+        if (batch > 0) {
+            DeviceGuard g(c->device);
+            spec_status sa = czt_auto_decide(c, batch, n, fs, f1, f2, m, &mode, (cudaStream_t)stream);
+            if (sa != SPEC_OK) return sa;
+        }
+    }
+    const bool gemm = mode == SPEC_CZT_GEMM_F16X3 || mode == SPEC_CZT_GEMM_F16X1 || mode == SPEC_CZT_GEMM_BF16X1;
     if (gemm && gemm_z_bytes(n, m) > (size_t(1) << 31))
         return fail(c, SPEC_EUNSUPPORTED, "GEMM chirp-z: Z above 2 GiB (use SPEC_CZT_BLUESTEIN)");
     std::string why, why_long;
@@ -634,7 +635,8 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
                                                  stream);
                              });
     if (gemm)
-        return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m, mode == SPEC_CZT_GEMM_F16X3 ? 3 : 1, X, ld_X, st);
+        return czt_gemm(c, x, batch, n, ld_x, fs, f1, f2, m,
+                        mode == SPEC_CZT_GEMM_F16X3 ? 3 : mode == SPEC_CZT_GEMM_F16X1 ? 1 : -1, X, ld_X, st);
     float2* X2 = reinterpret_cast<float2*>(X);
 
     // Bluestein tables for (N, M, f1/fs, step/fs), cached (for a segmented

@@ -55,13 +55,18 @@ struct FftPlan {
     bool dual = false;  // two residues per thread (packed lanes)
     bool paired = false;  // C > 1 CTAs own residue pairs {r, R - r}: no cluster, local unpack
     bool fixed = false;   // two-lane kernel compiled for this (LZ, R) with packed tables (C == 1)
+    bool clustered = false;  // one cluster of C CTAs per trace, conjugate-paired residues (k_fft_real_cluster)
     int emax = 16;      // elements per thread (16 or 32: radix of the passes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
     size_t smem = 0;
 };
 // Returns false (with a reason) if the size needs a path the library lacks.
-bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why);
+// allow_cluster = true plans k_fft_real_cluster where it has an instance;
+// it measured slower than the CTA-pair kernels on GB300 (2048 traces of 8192
+// samples to 65536 points: 728 against 500 us; 4096 x 4096 to 32768: 566
+// against 318 us), so only the ragged autotuner times it as a candidate.
+bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* why, bool allow_cluster = false);
 // Per-plan twiddles (pre-twiddle factors and the unpack twiddle; with
 // `fixed` also the packed two-lane pre-twiddles and BlockFFT twiddles),
 // float64 on the host, rounded to float.
@@ -148,8 +153,9 @@ cudaError_t long_czt_launch(const LongPlan& p, const CztTables& t, const float2*
 int gemm_padded_n(int64_t n);
 size_t gemm_z_bytes(int64_t n, int64_t m);          // Zh | Zl, FP16 [2M][ceil64(N)] each
 size_t gemm_work_bytes(int64_t batch, int64_t n);   // xh | xl | row exponents
-cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, cudaStream_t st);
-// terms 3: split FP16 (FP32-level accuracy); 1: one FP16 product.  The
+cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, cudaStream_t st, bool bf16 = false);
+// terms 3: split FP16 (FP32-level accuracy); 1: one FP16 product; -1: one
+// BF16 product (x and the BF16 Z table).  The
 // split writes x's FP16 parts and row exponents into `work`
 // (gemm_work_bytes(batch, n)); the product reads them.
 cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int terms, void* work,
@@ -188,6 +194,49 @@ cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_
                         int lanes);
 
 // ---- ragged batches (ragged.cu drives these) -------------------------------
+// Persistent chirp-z over a work queue (k_czt.cu): units of max(1, 8192/L)
+// traces of one Bluestein length L, largest L first; items[].tab_off is the offset of
+// the trace's FFT(v)/L in vpool (one per distinct (N, M, B)).
+struct CztUnit {
+    int L;          // Bluestein length of the unit's traces
+    int first;      // first item (index into the item array)
+    int count;      // traces in the unit (<= 16384 / L)
+    int pad;
+};
+// Persistent padded FFT over a work queue (k_fft.cu): mode 0 units hold
+// 512/(R/2 LZ/16) whole traces (H <= 16384), mode 1 units `count` residue
+// pairs g0 .. of one trace (item), mode 2 units one trace through a per-CTA
+// workspace; tab is the (LZ, R) plan's generic table.
+struct FftUnit {
+    const float2* tab;
+    int LZ, logR;
+    int item, count, g0, mode;
+};
+size_t fft_queue_smem();
+// ws: ctas x ws_per_cta complex values (mode 2 units: ws_per_cta >= H); the
+// grid has exactly `ctas` CTAs (each owns one workspace slot)
+cudaError_t fft_queue_launch(const RaggedItem* items, const FftUnit* units, int nunits, unsigned* counter,
+                             const float* x_pool, const float2* btw, float2* X_pool, float2* ws, int64_t ws_per_cta,
+                             int ctas, cudaStream_t st);
+// Persistent Zoom FFT over a work queue (k_zoom.cu): a unit is up to F
+// traces of one K <= 16384 (F <= 1024/(K/16)), trace f in the `slice`-byte
+// shared-memory slice f; thread groups without a trace use the FFT area at
+// byte `scratch` (valid when count < 1024/(K/16)).
+struct ZoomUnit {
+    int K, first, count, F;
+    int slice, scratch;
+};
+int zoom_queue_groups(int K);
+cudaError_t zoom_queue_launch(const RaggedItem* items, const ZoomUnit* units, int nunits, unsigned* counter,
+                              size_t smem, const float* x_pool, const float* taps_pool, const float2* tw,
+                              float2* X_pool, int ctas, cudaStream_t st);
+size_t czt_queue_smem();
+int czt_queue_unit_traces(int L);
+cudaError_t czt_vpool_build(int L, const RaggedItem* keys, int64_t count, float2* vpool, const float2* tw_base,
+                            cudaStream_t st);
+cudaError_t czt_queue_launch(const RaggedItem* items, const CztUnit* units, int nunits, unsigned* counter,
+                             const float* x_pool, const float2* vpool, const float2* tw_base, const float2* tw32_base,
+                             float2* X_pool, int ctas, cudaStream_t st);
 cudaError_t czt_ragged_tables(int L, const RaggedItem* items, int64_t count, float2* tables, const float2* tw,
                               cudaStream_t st);
 cudaError_t czt_ragged_launch(int L, const RaggedItem* items, int64_t count, const float* x_pool,

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libspec.so")
 
 SPEC_OK, SPEC_EINVAL, SPEC_ENOMEM, SPEC_ECUDA, SPEC_EUNSUPPORTED, SPEC_ETIMEOUT = range(6)
-SPEC_CZT_AUTO, SPEC_CZT_BLUESTEIN, SPEC_CZT_GEMM_F16X3, SPEC_CZT_GEMM_F16X1 = 0, 1, 2, 3
+SPEC_CZT_AUTO, SPEC_CZT_BLUESTEIN, SPEC_CZT_GEMM_F16X3, SPEC_CZT_GEMM_F16X1, SPEC_CZT_GEMM_BF16X1 = 0, 1, 2, 3, 4
 
 _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "SPEC_ECUDA",
            SPEC_EUNSUPPORTED: "SPEC_EUNSUPPORTED", SPEC_ETIMEOUT: "SPEC_ETIMEOUT"}
@@ -28,7 +28,7 @@ _STATUS = {SPEC_EINVAL: "SPEC_EINVAL", SPEC_ENOMEM: "SPEC_ENOMEM", SPEC_ECUDA: "
 EXPORTS = ("spec_ctx_create", "spec_ctx_destroy", "spec_last_error", "spec_ctx_check",
            "spec_selftest_wait_timeout", "spec_measure_fp32_peak",
            "spec_fft", "spec_czt", "spec_czt_spiral", "spec_zoom", "spec_czt_static", "spec_ragged",
-           "spec_ragged_launches",
+           "spec_ragged_launches", "spec_ragged_plan_info", "spec_czt_auto_mode", "spec_tune_cache_store", "spec_tune_cache_lookup",
            "spec_zeros_for_delta", "spec_m_for_resolution", "spec_design_lowpass")
 
 SPEC_KIND_FFT, SPEC_KIND_CZT, SPEC_KIND_ZOOM = 0, 1, 2
@@ -85,6 +85,15 @@ def lib():
     L.spec_ragged_launches.restype = i64
     L.spec_czt_static.argtypes = [fp, i64, i64, i64, dbl, dbl, dbl, i64, fp, i64, vp]
     L.spec_czt_static.restype = C.c_int
+    L.spec_ragged_plan_info.argtypes = [vp, C.c_int, C.POINTER(spec_desc), i64, dbl, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_float)]
+    L.spec_ragged_plan_info.restype = C.c_int
+    L.spec_czt_auto_mode.argtypes = [vp, i64, i64, dbl, dbl, dbl, i64, C.POINTER(C.c_int), vp]
+    L.spec_czt_auto_mode.restype = C.c_int
+    L.spec_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, C.c_char_p, C.c_char_p]
+    L.spec_tune_cache_store.restype = C.c_int
+    L.spec_tune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, C.c_char_p, C.c_char_p, C.c_int]
+    L.spec_tune_cache_lookup.restype = C.c_int
     L.spec_zeros_for_delta.argtypes = [dbl, i64, dbl]
     L.spec_zeros_for_delta.restype = i64
     L.spec_m_for_resolution.argtypes = [dbl, dbl, dbl, i64]
@@ -238,13 +247,12 @@ def spec_zoom(ctx: Context, x, fs: float, f1: float, f2: float, d: int, taps, n_
 
 
 def spec_ragged(ctx: Context, kind: int, descs, fs: float, x_pool, X_pool, taps_pool=None, stream=None):
-    """Ragged batch: descs is a sequence of spec_desc (or dicts of its fields);
-    pools are CUDA tensors (x float32, X complex64, taps float32)."""
+    """Ragged batch: descs is a sequence of spec_desc (or dicts of its fields),
+    or an array from ``desc_array`` (passed through without copying: build it
+    once for a batch that is transformed repeatedly); pools are CUDA tensors
+    (x float32, X complex64, taps float32)."""
     import torch
-    n = len(descs)
-    arr = (spec_desc * max(1, n))()
-    for i, dsc in enumerate(descs):
-        arr[i] = dsc if isinstance(dsc, spec_desc) else spec_desc(**dsc)
+    arr, n = _desc_array(descs)
     st = torch.cuda.current_stream(x_pool.device).cuda_stream if stream is None else stream
     ctx.check(lib().spec_ragged(ctx.handle, int(kind), arr, n, float(fs), x_pool.data_ptr(),
                                 taps_pool.data_ptr() if taps_pool is not None else None,
@@ -252,17 +260,63 @@ def spec_ragged(ctx: Context, kind: int, descs, fs: float, x_pool, X_pool, taps_
     return X_pool
 
 
+class DescArray:
+    """A ctypes array of spec_desc built once (see desc_array)."""
+
+    def __init__(self, descs):
+        n = len(descs)
+        self.arr = (spec_desc * max(1, n))()
+        for i, dsc in enumerate(descs):
+            self.arr[i] = dsc if isinstance(dsc, spec_desc) else spec_desc(**dsc)
+        self.n = n
+
+    def __len__(self):
+        return self.n
+
+
+def desc_array(descs) -> DescArray:
+    """Marshal a descriptor list once, for repeated spec_ragged calls."""
+    return DescArray(descs)
+
+
 def _desc_array(descs):
-    n = len(descs)
-    arr = (spec_desc * max(1, n))()
-    for i, dsc in enumerate(descs):
-        arr[i] = dsc if isinstance(dsc, spec_desc) else spec_desc(**dsc)
-    return arr, n
+    if isinstance(descs, DescArray):
+        return descs.arr, descs.n
+    d = DescArray(descs)
+    return d.arr, d.n
 
 
 def spec_ragged_launches(ctx: Context, kind: int, descs, fs: float) -> int:
     arr, n = _desc_array(descs)
     return int(lib().spec_ragged_launches(ctx.handle, int(kind), arr, n, float(fs)))
+
+
+def spec_czt_auto_mode(ctx: Context, batch: int, n: int, fs: float, f1: float, f2: float, m: int,
+                       stream=None) -> int:
+    """The explicit mode SPEC_CZT_AUTO stands for at (batch, n, m)."""
+    out = C.c_int(0)
+    ctx.check(lib().spec_czt_auto_mode(ctx.handle, int(batch), int(n), float(fs), float(f1), float(f2), int(m),
+                                       C.byref(out), _stream_handle(stream)))
+    return out.value
+
+
+def spec_tune_cache_store(path: str, device: str, key: str, value: str) -> int:
+    return int(lib().spec_tune_cache_store(path.encode(), device.encode(), key.encode(), value.encode()))
+
+
+def spec_tune_cache_lookup(path: str, device: str, key: str):
+    """The cached value, or None."""
+    buf = C.create_string_buffer(256)
+    found = lib().spec_tune_cache_lookup(path.encode(), device.encode(), key.encode(), buf, 256)
+    return buf.value.decode() if found else None
+
+
+def spec_ragged_plan_info(ctx: Context, kind: int, descs, fs: float):
+    """(uses the work queue?, queue us, per-shape us) of the cached plan, or None."""
+    arr, n = _desc_array(descs)
+    tq, tc = C.c_float(0.0), C.c_float(0.0)
+    r = int(lib().spec_ragged_plan_info(ctx.handle, int(kind), arr, n, float(fs), C.byref(tq), C.byref(tc)))
+    return None if r < 0 else (bool(r), tq.value, tc.value)
 
 
 # ---------------------------------------------------------------- helpers ---

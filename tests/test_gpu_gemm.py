@@ -88,6 +88,22 @@ def test_gemm_f16x1_is_the_low_precision_form(ctx, S):
     assert err.max() > 1e-6           # it really is the one-product form
 
 
+def test_gemm_bf16x1_is_the_single_term_bf16_error(ctx, S):
+    # x and Z rounded once to BF16 (8-bit significands, unit roundoff 2^-9),
+    # one product accumulated in FP32: relative error of order 1e-3 per
+    # spectrum, several times the FP16 one-product form's (11-bit significands)
+    x = noise(64, 1024, 2)
+    ref = O.czt(x, FS, 0.8e12, 1.2e12, 512)
+    got = S.spec_czt(ctx, dev(x), FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_BF16X1).cpu().numpy()
+    f16 = S.spec_czt(ctx, dev(x), FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X1).cpu().numpy()
+    err, err16 = rel(got, ref), rel(f16, ref)
+    assert 3e-4 < err.max() <= 2e-2
+    assert err.mean() > 3 * err16.mean()
+    # the FP16 split form stays at the FP32 level on the same traces
+    split = S.spec_czt(ctx, dev(x), FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
+    assert rel(split, ref).max() <= 1e-5
+
+
 def test_gemm_matches_bluestein(ctx, S):
     x = dev(noise(256, 1024, 3))
     g = S.spec_czt(ctx, x, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3).cpu().numpy()
@@ -151,16 +167,43 @@ def test_bounded_wait_reports_timeout_and_context_survives(ctx, S):
     assert rel(got, O.czt(x, FS, 0.5e12, 1.0e12, 64)).max() <= TOL
 
 
-def test_auto_mode_choice(ctx, S):
-    # workload-3 shape: AUTO takes the split-FP16 GEMM; workload-1 shape: Bluestein
+def test_auto_mode_is_measured_and_equals_the_chosen_mode(ctx, S):
+    # AUTO's choice comes from timing both exact forms on a probe batch; the
+    # spectra of an AUTO call equal those of the explicit chosen mode bit for
+    # bit.  At the workload-3 shape (65536 x 1024, M = 512) the product wins;
+    # at the workload-1 shape (4096 x 2048, M = 1024, L = 4096) Bluestein does.
     x3 = dev(np.tile(noise(1024, 1024, 5), (64, 1)))
+    m3 = S.spec_czt_auto_mode(ctx, x3.shape[0], 1024, FS, 0.8e12, 1.2e12, 512)
     a = S.spec_czt(ctx, x3, FS, 0.8e12, 1.2e12, 512)
-    g = S.spec_czt(ctx, x3, FS, 0.8e12, 1.2e12, 512, mode=S.SPEC_CZT_GEMM_F16X3)
+    g = S.spec_czt(ctx, x3, FS, 0.8e12, 1.2e12, 512, mode=m3)
     assert torch.equal(torch.view_as_real(a), torch.view_as_real(g))
+    assert m3 == S.SPEC_CZT_GEMM_F16X3
     x1 = dev(noise(4096, 2048, 6))
+    m1 = S.spec_czt_auto_mode(ctx, 4096, 2048, FS, 0.2e12, 2.5e12, 1024)
     a = S.spec_czt(ctx, x1, FS, 0.2e12, 2.5e12, 1024)
-    b = S.spec_czt(ctx, x1, FS, 0.2e12, 2.5e12, 1024, mode=S.SPEC_CZT_BLUESTEIN)
+    b = S.spec_czt(ctx, x1, FS, 0.2e12, 2.5e12, 1024, mode=m1)
     assert torch.equal(torch.view_as_real(a), torch.view_as_real(b))
+    assert m1 == S.SPEC_CZT_BLUESTEIN
+
+
+def test_auto_mode_decisions_persist_to_the_cache_file(S, tmp_path, monkeypatch):
+    import json
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("SPEC_AUTOTUNE_CACHE", str(path))
+    with S.Context(0) as c:
+        mode = S.spec_czt_auto_mode(c, 8192, 1024, FS, 0.8e12, 1.2e12, 512)
+    d = json.loads(path.read_text())
+    assert d["format"] == "spec-autotune-1"
+    (key, value), = d["entries"].items()
+    assert key == "czt n=1024 m=512 b=8192"
+    assert value == ("gemm_f16x3" if mode == S.SPEC_CZT_GEMM_F16X3 else "bluestein")
+    # a new context reads the decision instead of measuring; a planted value
+    # shows that the file, not a new measurement, decided
+    planted = "bluestein" if value == "gemm_f16x3" else "gemm_f16x3"
+    assert S.spec_tune_cache_store(str(path), d["device"], key, planted) == 0
+    with S.Context(0) as c:
+        again = S.spec_czt_auto_mode(c, 8192, 1024, FS, 0.8e12, 1.2e12, 512)
+    assert again == (S.SPEC_CZT_GEMM_F16X3 if planted == "gemm_f16x3" else S.SPEC_CZT_BLUESTEIN)
 
 
 def test_gemm_large_batch_matches_small_calls(ctx, S):

@@ -54,6 +54,12 @@ FFT_CASES = [
 ]
 
 
+# traces that need a cluster of 2-8 CTAs (R LZ/8192 of them): every (LZ, R)
+# of the cluster kernel, full and partial traces
+FFT_CASES += [(2, 4000, 32768), (2, 8000, 32768), (2, 2000, 32768), (2, 1500, 65536), (2, 3000, 65536),
+              (1, 5000, 131072), (2, 1025, 65536), (3, 2049, 65536)]
+
+
 # N_FFT not a power of two (the resolution fs/N_FFT of Eq. 3 chosen freely):
 # the chirp-z on the DFT grid; the paper's unpadded 500-sample trace among them
 FFT_CASES += [(3, 500, 500), (2, 500, 1000), (2, 2048, 20000), (3, 1000, 12345), (2, 7, 9), (3, 100, 101),
@@ -292,3 +298,22 @@ def test_cluster_paths_under_full_occupancy(ctx, S, kind):
     got = got.reshape(150, 8, -1)
     assert (got == got[:1]).all()
     assert rel_rows(got[0], ref).max() <= TOL
+
+
+# ------------------------------------------------ the cluster FFT kernel ------
+
+CLUSTER_CASES = [(2, 4000, 32768), (2, 8000, 32768), (2, 2000, 32768), (2, 1500, 65536), (2, 3000, 65536),
+                 (1, 5000, 131072), (2, 1025, 65536), (3, 2049, 65536), (2, 8192, 65536), (2, 4096, 32768)]
+
+
+def test_fft_cluster_kernel_parity(S, monkeypatch):
+    # SPEC_FFT_CLUSTER=1 (read when a context is created) puts every (LZ, R)
+    # the cluster kernel has an instance for on it: conjugate-paired residues,
+    # spectrum assembled in the cluster's shared memory
+    monkeypatch.setenv("SPEC_FFT_CLUSTER", "1")
+    with S.Context(0) as c:
+        for batch, n, n_fft in CLUSTER_CASES:
+            x = traces(batch, n, n + n_fft)
+            got = S.spec_fft(c, dev(x), 20e12, n_fft).cpu().numpy()
+            err = rel_rows(got, O.fft_padded(x, n_fft))
+            assert err.max() <= TOL, (batch, n, n_fft, err.max())

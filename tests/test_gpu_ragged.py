@@ -1,10 +1,10 @@
 """Ragged batches (spec_ragged): traces with their own length, band, point
 count, decimation and taps in one call.  Every trace must match the same
-trace run alone through spec_fft / spec_czt / spec_zoom to 1e-6 relative L2
-(the same kernels and tables, except that the plan's autotuner may pick a
-different variant -- lanes or pass radix -- whose rounding differs in the last
-bits), and a sample is checked against the FP64 oracle (relative L2 <= 1e-5
-per spectrum).  The plan's CUDA graph replay is bit-identical to its first
+trace run alone through spec_fft / spec_czt / spec_zoom to 2e-6 relative L2
+(the plan's autotuner may pick a different kernel variant -- lanes, pass
+radix, cluster -- and the ragged chirp-z evaluates its chirps in the kernel,
+so the rounding differs in the last bits), and every trace is checked
+against the FP64 oracle (relative L2 <= 1e-5 per spectrum).  The plan's CUDA graph replay is bit-identical to its first
 run, and the graph is re-captured when the pools move."""
 import numpy as np
 import pytest
@@ -80,7 +80,19 @@ def single(S, ctx, kind, it, x, h):
     return S.spec_zoom(ctx, xd, FS, it.f1, it.f2, it.d, torch.from_numpy(h).cuda(), it.n_fft)[0]
 
 
+_ORACLE = {}
+
+
 def oracle(kind, it, x, h):
+    """The FP64 oracle's spectrum, computed once per (kind, trace) and reused
+    by the tests that check both forms of a plan."""
+    key = (kind, it.n, it.n_fft, it.f1, it.f2, it.m, it.d, it.n_taps, x.tobytes(), np.asarray(h).tobytes())
+    if key not in _ORACLE:
+        _ORACLE[key] = _oracle(kind, it, x, h)
+    return _ORACLE[key]
+
+
+def _oracle(kind, it, x, h):
     if kind == 0:
         return O.fft_padded(x, it.n_fft)[0]
     if kind == 1:
@@ -88,13 +100,33 @@ def oracle(kind, it, x, h):
     return O.zoom(x, FS, it.f1, it.f2, it.d, h, it.n_fft)[0]
 
 
+@pytest.fixture(scope="module")
+def forced(S):
+    """Contexts whose ragged plans always (1) or never (0) use the work
+    queue (SPEC_RAGGED_QUEUE is read when a context is created)."""
+    import os
+    out = {}
+    for v in (1, 0):
+        os.environ["SPEC_RAGGED_QUEUE"] = str(v)
+        out[v] = S.Context(0)
+    del os.environ["SPEC_RAGGED_QUEUE"]
+    yield out
+    for c in out.values():
+        c.close()
+
+
+@pytest.mark.parametrize("form", ["queue", "classes"])
 @pytest.mark.parametrize("kind", [0, 1, 2])
-def test_ragged_matches_single_calls_and_oracle(S, ctx, kind):
+def test_ragged_matches_single_calls_and_oracle(S, ctx, forced, kind, form):
+    # both forms a plan can take: the persistent work queue and the per-shape
+    # launches, each against single calls and (every trace) the oracle
+    rc = forced[1 if form == "queue" else 0]
     items, traces = workload(48)
     descs, x_pool, X_pool, taps_pool, bins, taps = pools(items, traces, kind)
-    S.spec_ragged(ctx, kind, descs, FS, x_pool, X_pool, taps_pool)
+    S.spec_ragged(rc, kind, descs, FS, x_pool, X_pool, taps_pool)
+    assert S.spec_ragged_plan_info(rc, kind, descs, FS)[0] == (form == "queue")
     first = X_pool.clone()
-    S.spec_ragged(ctx, kind, descs, FS, x_pool, X_pool, taps_pool)      # graph replay
+    S.spec_ragged(rc, kind, descs, FS, x_pool, X_pool, taps_pool)       # graph replay
     torch.cuda.synchronize()
     assert torch.equal(torch.view_as_real(first), torch.view_as_real(X_pool))
     got = X_pool.cpu().numpy()
@@ -102,11 +134,10 @@ def test_ragged_matches_single_calls_and_oracle(S, ctx, kind):
         o, nb = descs[i]["out_off"], bins[i]
         ref = single(S, ctx, kind, it, traces[i], taps[i]).cpu().numpy()
         d = np.linalg.norm(got[o:o + nb] - ref) / np.linalg.norm(ref)
-        assert d <= 1e-6, (i, d)
-        if i < 6 or i % 8 == 0:
-            r = oracle(kind, it, traces[i], taps[i])
-            err = np.linalg.norm(got[o:o + nb] - r) / np.linalg.norm(r)
-            assert err <= TOL, (i, err)
+        assert d <= 2e-6, (i, d)
+        r = oracle(kind, it, traces[i], taps[i])
+        err = np.linalg.norm(got[o:o + nb] - r) / np.linalg.norm(r)
+        assert err <= TOL, (i, err)
 
 
 def test_ragged_recaptures_when_pools_move(S, ctx):
@@ -147,3 +178,35 @@ def test_ragged_czt_odd_class_with_two_traces_per_cta(S, ctx):
         o, nb = descs[i]["out_off"], bins[i]
         r = oracle(1, it, traces[i], taps[i])
         assert np.linalg.norm(got[o:o + nb] - r) / np.linalg.norm(r) <= TOL
+
+
+def test_ragged_czt_queue_units_and_shared_kernel_spectra(S, forced):
+    ctx = forced[1]
+    # The chirp-z work queue packs 8192/L traces per unit: 1030 traces of
+    # L = 16 make three units (the last with dead slots), mixed with longer
+    # classes; repeated (N, M, band) share one FFT(v)/L table.  Every trace
+    # must match the oracle, and the repeats must equal their originals.
+    rng = np.random.default_rng(11)
+    items = []
+    for i in range(1030):
+        items.append(synth.RaggedTrace(5, 64, 0.1e12 + 1e9 * (i % 7), 3.0e12, 8, 2, 31))
+    for i in range(9):
+        n = int(rng.integers(1000, 8193))
+        items.append(synth.RaggedTrace(n, 65536, 0.3e12, 0.3e12 + 0.1e12 * (i + 1), int(rng.integers(256, 4097)),
+                                       2, 31))
+    items.append(items[-1])
+    # standard-normal samples: 5-sample THz traces would be all zero
+    traces = [rng.standard_normal(it.n).astype(np.float32) for it in items]
+    traces[-1] = traces[-2]
+    descs, x_pool, X_pool, taps_pool, bins, taps = pools(items, traces, 1)
+    S.spec_ragged(ctx, 1, descs, FS, x_pool, X_pool, taps_pool)
+    torch.cuda.synchronize()
+    got = X_pool.cpu().numpy()
+    assert S.spec_ragged_launches(ctx, 1, descs, FS) == 1
+    for i in list(range(0, 1030, 37)) + [1029] + list(range(1030, len(items))):
+        it = items[i]
+        o, nb = descs[i]["out_off"], bins[i]
+        r = oracle(1, it, traces[i], taps[i])
+        assert np.linalg.norm(got[o:o + nb] - r) / np.linalg.norm(r) <= TOL, i
+    o1, o2 = descs[-2]["out_off"], descs[-1]["out_off"]
+    assert np.array_equal(got[o1:o1 + bins[-2]], got[o2:o2 + bins[-1]])
