@@ -791,7 +791,8 @@ def measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, scaling):
         rg = synth.ragged_params(total)
         costs = [shard.ragged_trace_cost(it.n, it.n_fft, it.m, it.d, it.n_taps) for it in rg.items]
         parts_idx = shard.balance_by_cost(costs, world)
-        W = Ragged(spec, ctx, dev, count=len(parts_idx[rank]), indices=parts_idx[rank], total=total)
+        mine = parts_idx[rank] if args.batch is None else parts_idx[rank][:int(args.batch)]
+        W = Ragged(spec, ctx, dev, count=len(mine), indices=mine, total=total)
         share = {"traces": len(parts_idx[rank]), "of": total, "split": "cost-balanced (greedy LPT)",
                  "imbalance": shard.imbalance(costs, parts_idx)}
     else:
@@ -857,11 +858,19 @@ def measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, scaling):
         g_ms = kern["czt"]["ms"]
         cmp = {"gemm_mode": "SPEC_CZT_GEMM_F16X3", "gemm_ms": g_ms, "bluestein_fp32_ms": b_ms,
                "factor": b_ms / g_ms, "what": "same 65536-trace batch, L2 flushed, CUDA events"}
+        # the single-term BF16 product (x and Z rounded once to BF16): its
+        # error, reported beside the split form's
+        xbf = torch.empty_like(W.out["czt"])
+        bf = [("czt_bf16x1", lambda: spec.spec_czt(ctx, W.xd, cfg.fs, cfg.czt_f1, cfg.czt_f2, cfg.czt_m,
+                                                   mode=spec.SPEC_CZT_GEMM_BF16X1, out=xbf))]
+        cmp["bf16x1_ms"] = statistics.median(timed_parts(bf, max(5, min(steps, 20)), args.warmup, flush,
+                                                         stream)["czt_bf16x1"])
         if want_cpu:
-            cmp["gemm_rel_l2"] = kern["czt"].get("max_rel_l2_sampled")
+            cmp["gemm_rel_l2"] = kern["czt"].get("max_rel_l2_all_traces", kern["czt"].get("max_rel_l2_sampled"))
             cmp["bluestein_rel_l2"] = W.rel_l2_vs_oracle(xb)
+            cmp["bf16x1_rel_l2"] = W.rel_l2_vs_oracle(xbf)
         res["czt_gemm_vs_bluestein"] = cmp
-        del xb
+        del xb, xbf
     res["_W"] = W
     return res
 
@@ -1016,8 +1025,8 @@ def main(argv=None):
                     help="where to write the clock samples of the timed region ({rank} is replaced); "
                          "default: the temp directory")
     ap.add_argument("--batch", type=int, default=None,
-                    help="traces per step for workloads 1, 3 and 4 (a smaller case for profiling; "
-                         "the default is the workload's batch)")
+                    help="traces per step (a smaller case for profiling; the default is the workload's batch; "
+                         "for workload 2 the first traces of the rank's share)")
     args = ap.parse_args(argv)
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         return relaunch_under_torchrun(args, argv)

@@ -122,6 +122,20 @@ SPEC_API spec_status spec_measure_fp32_peak(spec_ctx* ctx, double* tflops, void*
 SPEC_API spec_status spec_selftest_wait_timeout(spec_ctx* ctx, int64_t timeout_us, void* stream);
 
 /*
+ * Kernel variants.  spec_fft, spec_czt (Bluestein) and spec_zoom have
+ * several kernels for one shape (two traces or residues per thread as packed
+ * lanes or one; for the FFT also a kernel compiled for the shape, and a
+ * cluster kernel for long traces).  The first call with a device-resident
+ * batch of a given shape runs each variant three times on the call's own
+ * buffers, keeps the fastest for that shape (every later call, and every
+ * chunk of a host-buffer call, runs the same arithmetic) and so synchronises
+ * `stream` once; the choice is also stored in the SPEC_AUTOTUNE_CACHE file
+ * (see spec_czt_auto_mode).  During stream capture nothing is timed and the
+ * first variant runs.  SPEC_LANES=1 or 2 in the environment at context
+ * creation pins the lanes instead.
+ */
+
+/*
  * Zero-padded FFT of real traces (Section 2.1, Eq. 2 with the forward sign
  * e^{-j 2 pi k n / N_FFT}; the zero-padding paragraph; resolution
  * Delta f = fs/N_FFT, Eq. 3):

@@ -23,6 +23,8 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <functional>
+#include <vector>
 #include <map>
 #include <sstream>
 #include <string>
@@ -255,6 +257,12 @@ spec_status czt_auto_decide(spec_ctx* c, int64_t batch, int64_t n, double fs, do
         return SPEC_OK;
     }
     *mode = SPEC_CZT_BLUESTEIN;
+    // under stream capture nothing can be measured: Bluestein, not remembered
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return SPEC_OK;
+    }
     // the product is a candidate when its Z table fits and the batch fills
     // the GPU with output tiles; a model far on Bluestein's side skips it
     bool candidate = gemm_z_bytes(n, m) <= (size_t(1) << 31) &&
@@ -341,3 +349,80 @@ extern "C" int spec_tune_cache_lookup(const char* path, const char* device, cons
     }
     return 1;
 }
+
+// ------------------------------------------------- kernel variant choices --
+
+namespace spec {
+
+// The fastest of `names` for `key`: remembered, read from the cache file, or
+// measured now by running each candidate three times on the caller's own
+// device buffers (the chosen variant then overwrites the output; the first
+// run of each is discarded).  Synchronises `st` when it measures.  Returns
+// the index into `names`, or -1 with *status set if a candidate fails.
+int tune_pick(spec_ctx* c, const std::string& key, const std::vector<std::string>& names,
+              const std::function<cudaError_t(int)>& run, cudaStream_t st, spec_status* status) {
+    *status = SPEC_OK;
+    if (names.size() == 1) return 0;
+    auto it = c->tune.find(key);
+    if (it != c->tune.end())
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == it->second) return (int)i;
+    // nothing can be timed while the stream is being captured into a graph:
+    // the first candidate, nothing remembered
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaEvent_t ea, eb;
+    if (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) {
+        cudaGetLastError();
+        *status = SPEC_ECUDA;
+        return -1;
+    }
+    int best = -1;
+    float best_ms = 1e30f;
+    for (size_t i = 0; i < names.size(); ++i) {
+        float t = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(ea, st);
+            const cudaError_t e = run((int)i);
+            cudaEventRecord(eb, st);
+            if (e != cudaSuccess || cudaEventSynchronize(eb) != cudaSuccess) {
+                cudaGetLastError();
+                t = 1e30f;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ea, eb);
+            if (r > 0) t = std::min(t, ms);
+        }
+        if (t < best_ms) {
+            best_ms = t;
+            best = (int)i;
+        }
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (best < 0) {
+        *status = SPEC_ECUDA;
+        return -1;
+    }
+    c->tune[key] = names[(size_t)best];
+    if (!c->tune_path.empty()) tune_file_store(c->tune_path, c->tune_device, key, names[(size_t)best]);
+    return best;
+}
+
+// "what v0:v1:..." (the shape a decision belongs to)
+std::string tune_key(const char* what, std::initializer_list<long long> v) {
+    std::string k = std::string(what) + " ";
+    bool first = true;
+    for (long long x : v) {
+        if (!first) k += ":";
+        k += std::to_string(x);
+        first = false;
+    }
+    return k;
+}
+
+}  // namespace spec

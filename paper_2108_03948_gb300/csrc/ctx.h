@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <string>
@@ -23,9 +25,10 @@ struct CztEntry {
 };
 
 struct FftEntry {
-    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables, 2: multi-pass twiddles (H = period log2)
+    int kind = 0;        // 0: padded real FFT tables, 1: pruned complex FFT tables, 2: multi-pass twiddles (H = period log2),
+                         // 4: mixed-radix padded FFT tables
     int H = 0, LZ = 0, emax = 16;
-    int layout = 0;      // kind 0: generic (0), fixed two-lane (1) or cluster (2) table layout
+    int layout = 0;      // kind 0: generic (0), fixed two-lane (1), cluster (2) or fused-unpack (3) table layout
     float2* tab = nullptr;
 };
 
@@ -50,6 +53,7 @@ struct spec_ctx {
     int lanes = 0;                       // 0: per transform (two packed lanes for the padded FFT, one for the
                                          // chirp-z and Zoom: measured fastest); 1 or 2: forced everywhere
     bool fft_cluster = false;            // SPEC_FFT_CLUSTER=1: long traces on k_fft_real_cluster
+    std::string fft_variant;             // SPEC_FFT_VARIANT: pin a padded-FFT kernel variant by name
     int ragged_queue = -1;               // SPEC_RAGGED_QUEUE: 1 always / 0 never the work queue, -1 timed
     std::map<std::string, std::string> tune;   // SPEC_CZT_AUTO decisions ("czt n=.. m=.. b=.." -> mode)
     std::string tune_path, tune_device;        // SPEC_AUTOTUNE_CACHE file and this device's tag
@@ -82,6 +86,12 @@ bool tune_file_write(const std::string& path, const std::string& device,
 bool tune_file_store(const std::string& path, const std::string& device, const std::string& key,
                      const std::string& value);
 std::string device_tag(int device);
+// the fastest of `names` for `key` (remembered, cached on file, or measured
+// by `run(i)` on the caller's buffers); -1 with *status set on failure
+int tune_pick(spec_ctx* c, const std::string& key, const std::vector<std::string>& names,
+              const std::function<cudaError_t(int)>& run, cudaStream_t st, spec_status* status);
+// "what v0:v1:..." -- the shape a variant decision belongs to
+std::string tune_key(const char* what, std::initializer_list<long long> v);
 spec_status czt_auto_decide(spec_ctx* c, int64_t batch, int64_t n, double fs, double f1, double f2, int64_t m,
                             int* mode, cudaStream_t st);
 }  // namespace spec

@@ -284,6 +284,37 @@ __host__ __device__ constexpr float cos_pi16(int k) {
          : k == 6 ? 0.38268343236508977173f : k == 7 ? 0.19509032201612826785f : 0.0f;
 }
 
+// cos(pi k/32), k = 0 .. 16
+__host__ __device__ constexpr float cos_pi32(int k) {
+    return k == 0 ? 1.0f : k == 1 ? 0.99518472667219688624f : k == 2 ? 0.98078528040323044913f
+         : k == 3 ? 0.95694033573220886494f : k == 4 ? 0.92387953251128675613f : k == 5 ? 0.88192126434835502971f
+         : k == 6 ? 0.83146961230254523708f : k == 7 ? 0.77301045336273696081f : k == 8 ? 0.70710678118654752440f
+         : k == 9 ? 0.63439328416364549822f : k == 10 ? 0.55557023301960222474f : k == 11 ? 0.47139673682599764856f
+         : k == 12 ? 0.38268343236508977173f : k == 13 ? 0.29028467725446236764f : k == 14 ? 0.19509032201612826785f
+         : k == 15 ? 0.09801714032956060199f : 0.0f;
+}
+// cos(pi a/32) for any integer a (period 64, even, cos(pi - x) = -cos x)
+__host__ __device__ constexpr float cos_pi32_any(int a) {
+    return (a % 64 + 64) % 64 <= 16 ? cos_pi32((a % 64 + 64) % 64)
+         : (a % 64 + 64) % 64 <= 32 ? -cos_pi32(32 - (a % 64 + 64) % 64)
+         : (a % 64 + 64) % 64 <= 48 ? -cos_pi32((a % 64 + 64) % 64 - 32)
+         : cos_pi32(64 - (a % 64 + 64) % 64);
+}
+// e^{-j pi a/32} (sin x = cos(x - pi/2))
+__host__ __device__ constexpr float2 wpi32(int a) { return float2{cos_pi32_any(a), -cos_pi32_any(a - 16)}; }
+// w e^{-j pi a/32}, exact for multiples of pi/2
+template <int A> __device__ __forceinline__ float2 rot_pi32(float2 w) {
+    constexpr int q = ((A % 64) + 64) % 64;
+    if constexpr (q == 0) return w;
+    else if constexpr (q == 16) return make_float2(w.y, -w.x);
+    else if constexpr (q == 32) return make_float2(-w.x, -w.y);
+    else if constexpr (q == 48) return make_float2(-w.y, w.x);
+    else {
+        constexpr float c = cos_pi32_any(q), sn = cos_pi32_any(q - 16);
+        return make_float2(fmaf(w.x, c, w.y * sn), fmaf(w.y, c, -w.x * sn));
+    }
+}
+
 // 32 = 2 x 16: X[k] = E[k] + w32^k O[k], X[k + 16] = E[k] - w32^k O[k]
 template <bool INV, class V> __device__ __forceinline__ void dft32(V* a) {
     V e[16], o[16];
@@ -432,6 +463,23 @@ template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typenam
 
     static __device__ __forceinline__ void run(V (&v)[E], SM* s, int t, const TW* tw) {
         passes<0>(v, s, t, tw);
+    }
+
+    // Passes 0 .. NP-1 only (compute and the exchanges between them): the
+    // caller fuses the remaining passes into its own data movement.  Thread t
+    // then holds the outputs of pass NP-1 that exchange<NP-1> would store.
+    template <int P, int NP>
+    static __device__ __forceinline__ void passes_until(V (&v)[E], SM* s, int t, const TW* tw) {
+        if constexpr (P < NP) {
+            if constexpr (P > 0) exchange<P - 1>(v, s, t);
+            compute<P>(v, t, tw);
+            passes_until<P + 1, NP>(v, s, t, tw);
+        }
+    }
+    template <int NP>
+    static __device__ __forceinline__ void run_first(V (&v)[E], SM* s, int t, const TW* tw) {
+        static_assert(NP >= 1 && NP <= S::NPASS, "pass count");
+        passes_until<0, NP>(v, s, t, tw);
     }
 };
 

@@ -562,6 +562,189 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2r(FftArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Two-lane kernel with the last Stockham pass fused into the unpack, for
+// (LZ, R) whose BlockFFT<LZ> has three passes (radix 16, 16, rho; LZ = 512
+// has rho = 2, LZ = 1024 rho = 4).  The kernels above run all three passes,
+// store Z to shared memory and read it back for the unpack; here the outputs
+// of the second pass go straight to the staging area, and each unpack thread
+// computes the rho-point butterflies whose outputs it needs:
+//
+//   Z[k + n H/rho] (n < rho) are the outputs of butterfly j = k/R of residue
+//   r = k mod R, and their mirrors Z[H - k - n H/rho] are the outputs of one
+//   butterfly of residue R - r (of residue 0 for r = 0), whose inputs sit at
+//   staging slots (m + 1) H/rho - k.  So one thread reads 2 rho values,
+//   computes two butterflies and forms the 2 rho outputs X[k + n H/rho] and
+//   X[H - k - n H/rho] (k < H/(2 rho)), every Z value read once.
+//
+// That removes one shared-memory exchange of the whole trace and the third
+// pass's twiddle loads, which matters because the two-lane kernels are bound
+// by the L1 / shared-memory data pipe (ncu: lsu wavefronts at 84% of peak),
+// not by DRAM.  Lanes a and b carry residues 2p and 2p + 1, so the staged
+// pair is one 16-byte store; the staging slot of x = pos R + r (float2 units)
+// XORs the 16-byte chunk index within each 128-byte row with the row index
+// (mod 8), which keeps the stride-R stores and the consecutive-k reads free
+// of bank conflicts without padding.
+//
+// Table (float4 units): pre4 [R/2][LZ] = (wa.x, wb.x, wa.y, wb.y),
+// wa = w_H^{2p m}, wb = w_H^{(2p+1) m}; BlockFFT<LZ> twiddles (c, c, s, s);
+// ub4 [PT] = (w_{2H}^{lt}/2, w_LZ^{lt/R}); then (float2 units) um [PT] =
+// w_LZ^{j'(lt)}, the mirror butterfly index of k = lt.  The per-k twiddles
+// are these times compile-time constants (k = lt + PT j: w_{2H}^{PT j} =
+// e^{-j pi j/32}, w_LZ^{(PT/R) j} = e^{-j 2 pi j/32}).
+__host__ __device__ constexpr int fused_tw4_index(int LZ, int R) { return (R / 2) * LZ; }
+__host__ __device__ constexpr int fused_ub4_index(int LZ, int R) { return fused_tw4_index(LZ, R) + fft_twiddle_entries(LZ); }
+__host__ __device__ constexpr int fused_um_index(int LZ, int R) { return 2 * (fused_ub4_index(LZ, R) + (R / 2) * (LZ / 16)); }
+__host__ __device__ constexpr int fused_entries(int LZ, int R) { return fused_um_index(LZ, R) + (R / 2) * (LZ / 16); }
+// float2 per trace: the BlockFFT exchange areas of the R/2 pairs (the staged
+// H values fit in the same space)
+__host__ __device__ constexpr int fused_trace_smem(int LZ, int R) { return (R / 2) * padded_len(LZ) * 2; }
+
+// staging slot of x (float2 units)
+__device__ __forceinline__ int fsw(int x) { return x ^ (((x >> 4) & 7) << 1); }
+
+// b_m = y_m w^m, then the rho-point DFT in place (natural output order)
+template <int RHO>
+__device__ __forceinline__ void fused_butterfly(float2 (&y)[RHO], float2 w) {
+    if constexpr (RHO == 2) {
+        y[1] = cmul(y[1], w);
+        dft2<false>(y[0], y[1]);
+    } else {
+        const float2 w2 = cmul(w, w);
+        const float2 w3 = cmul(w2, w);
+        y[1] = cmul(y[1], w);
+        y[2] = cmul(y[2], w2);
+        y[3] = cmul(y[3], w3);
+        dft4<false>(y[0], y[1], y[2], y[3]);
+    }
+}
+
+template <int LZ, int R>
+__global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
+    using S = FFTShape<LZ, 16>;
+    static_assert(S::NPASS == 3 && S::NPB == 2, "fused kernel: radix 16, 16, rho");
+    constexpr int RHO = S::REM;
+    static_assert(RHO == 2 || RHO == 4, "fused butterflies of radix 2 or 4");
+    constexpr int T = LZ / 16, E = 16, G = R / 2, PT = G * T;
+    constexpr int F = PT >= 256 ? 1 : 256 / PT;
+    constexpr int H = R * LZ;
+    constexpr int HB = H / RHO;          // outputs k + n HB share a butterfly
+    constexpr int J = 16 / RHO;          // k values per thread
+    constexpr int TS = fused_trace_smem(LZ, R);
+    static_assert(PT * J * 2 * RHO == H, "every output once");
+    static_assert(PT % 128 == 0 && HB % 128 == 0, "staging swizzle constant along j and m");
+    static_assert(PT / R * 32 == LZ, "q steps by LZ/32 along j");
+    using FFT = BlockFFT<LZ, false, C2, 16, float4>;
+    extern __shared__ float4 smem4[];
+
+    const int tid = threadIdx.x;
+    const int f = tid / PT;
+    const int lt = tid - f * PT;
+    const int gl = lt / T;
+    const int t = lt - gl * T;
+    const int64_t b = (int64_t)blockIdx.x * F + f;
+    const bool live = b < a.batch;
+    int n = a.n;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+    }
+    float2* zs = reinterpret_cast<float2*>(smem4) + f * TS;
+    float4* s = reinterpret_cast<float4*>(zs) + gl * padded_len(LZ);
+    const float4* tab4 = reinterpret_cast<const float4*>(a.tab);
+
+    C2 v[E];
+    {
+        const float4* w4 = tab4 + gl * LZ + t;
+        const float* xr = a.x + xo;
+        if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
+            const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
+#pragma unroll
+            for (int i = 0; i < E; ++i) v[i] = pretwiddle2(__ldg(x2 + T * i), __ldg(w4 + T * i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int m = t + T * i;
+                float re = 0.f, im = 0.f;
+                if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+                if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+                v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
+            }
+        }
+    }
+    FFT::template run_first<2>(v, s, t, tab4 + fused_tw4_index(LZ, R));
+
+    // outputs of pass 1 (radix 16, span 16): v[r] is position base + 16 r of
+    // residues 2 gl and 2 gl + 1, staged at x = pos R + 2 gl
+    __syncthreads();
+    {
+        const int k16 = t & 15;
+        const int pos0 = (t - k16) * 16 + k16;
+        float4* st4 = reinterpret_cast<float4*>(zs);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int x = (pos0 + 16 * r) * R + 2 * gl;
+            st4[fsw(x) >> 1] = make_float4(v[r].re.x, v[r].im.x, v[r].re.y, v[r].im.y);
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+
+    float2* Xr = a.X + Xo;
+    const float4 ub = __ldg(tab4 + fused_ub4_index(LZ, R) + lt);
+    const float2 wk0 = make_float2(ub.x, ub.y);    // w_{2H}^{lt} / 2
+    const float2 wq0 = make_float2(ub.z, ub.w);    // w_LZ^{lt/R}
+    const float2 wm0 = __ldg(a.tab + fused_um_index(LZ, R) + lt);
+    // the swizzle depends only on the low 7 bits of x, and PT j, m HB are
+    // multiples of 128: every slot below is a base plus a constant
+    const float2* zf = zs + fsw(lt);
+    const float2* zm = zs + fsw(HB - lt) - HB;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        if (j == 0 && lt == 0) continue;           // k = 0: below
+        const float2 wq = cmul(wq0, wpi32(2 * j));   // w_LZ^{q}, q = k/R
+        const float2 wm = cmulc(wm0, wpi32(2 * j));  // w_LZ^{j'}, the mirror butterfly
+        const float2 wk = cmul(wk0, wpi32(j));        // w_{2H}^k / 2
+        float2 A[RHO], B[RHO];
+#pragma unroll
+        for (int m = 0; m < RHO; ++m) {
+            A[m] = zf[PT * j + m * HB];
+            B[m] = zm[(m + 1) * HB - PT * j];
+        }
+        fused_butterfly<RHO>(A, wq);               // A[n] = Z[k + n HB]
+        fused_butterfly<RHO>(B, wm);               // B[n] = Z[(n + 1) HB - k]
+        // pairs (k + n HB, H - k - n HB), twiddle w_{2H}^{k + n HB}/2
+        const int k = lt + PT * j;
+        unpack_pair_half<H>(Xr, k, A[0], B[RHO - 1], wk);
+        unpack_pair_half<H>(Xr, k + HB, A[1], B[RHO - 2], rot_pi32<32 / RHO>(wk));
+        if constexpr (RHO == 4) {
+            unpack_pair_half<H>(Xr, k + 2 * HB, A[2], B[1], rot_pi32<16>(wk));
+            unpack_pair_half<H>(Xr, k + 3 * HB, A[3], B[0], rot_pi32<24>(wk));
+        }
+    }
+    if (lt == 0) {
+        // k = 0: butterfly 0 of residue 0 (no twiddles): Z[n HB]
+        float2 A[RHO];
+#pragma unroll
+        for (int m = 0; m < RHO; ++m) A[m] = zs[fsw(m * HB)];
+        fused_butterfly<RHO>(A, make_float2(1.f, 0.f));
+        Xr[0] = make_float2(A[0].x + A[0].y, 0.f);
+        Xr[H] = make_float2(A[0].x - A[0].y, 0.f);
+        if constexpr (RHO == 4) unpack_pair_half<H>(Xr, HB, A[1], A[3], make_float2(0.5f * kS2, -0.5f * kS2));
+        Xr[H / 2] = make_float2(A[RHO / 2].x, -A[RHO / 2].y);
+        // k = HB/2: butterfly NS/2 of residue 0, twiddle w_LZ^{NS/2} = e^{-j pi/rho}
+#pragma unroll
+        for (int m = 0; m < RHO; ++m) A[m] = zs[fsw(HB / 2 + m * HB)];
+        fused_butterfly<RHO>(A, wpi32(32 / RHO));
+        // pairs (HB/2 + n HB, H - HB/2 - n HB), twiddle e^{-j pi (2n+1)/(2 rho)}/2
+        unpack_pair_half<H>(Xr, HB / 2, A[0], A[RHO - 1], cscale(wpi32(16 / RHO), 0.5f));
+        if constexpr (RHO == 4) unpack_pair_half<H>(Xr, HB / 2 + HB, A[1], A[2], cscale(wpi32(48 / RHO), 0.5f));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Traces too long for one CTA (R/2 residue pairs of LZ/16 threads exceed 256
 // threads): a thread-block cluster of C CTAs per trace, each CTA computing
 // 256/(LZ/16) residue pairs, and the spectrum assembled in the CTAs' shared
@@ -1228,17 +1411,27 @@ static FftKernel fft_kernel2_for(int LZ) {
 
 // (LZ, R) pairs with a compiled fixed two-lane kernel.  Measured on GB300:
 // 65536 traces of 1024 samples to 8192 points (LZ 512, R 8) 801 -> 775 us;
-// 4096 traces of 2048 samples to 16384 points (LZ 1024, R 8) 109 -> 113 us,
-// so that size keeps the generic two-lane kernel.
+// 4096 traces of 2048 samples to 16384 points (LZ 1024, R 8) 109 -> 113 us
+// (spec_fft times the variants of a shape and keeps the faster).
 static FftKernel fft_kernel_fixed_for(int LZ, int R) {
 #define SPEC_FIXED(lz, r) if (LZ == lz && R == r) return k_fft_real_padded2r<lz, r>;
-    SPEC_FIXED(256, 8) SPEC_FIXED(512, 8)
+    SPEC_FIXED(256, 8) SPEC_FIXED(512, 8) SPEC_FIXED(1024, 8)
     SPEC_FIXED(512, 4) SPEC_FIXED(1024, 4) SPEC_FIXED(2048, 4)
     SPEC_FIXED(256, 16) SPEC_FIXED(512, 16)
     SPEC_FIXED(1024, 2) SPEC_FIXED(2048, 2) SPEC_FIXED(4096, 2)
 #undef SPEC_FIXED
     return nullptr;
 }
+
+// (LZ, R) pairs with a compiled fused-unpack kernel (three-pass BlockFFT,
+// R/2 LZ/16 threads per trace a multiple of 128)
+static FftKernel fft_kernel_fused_for(int LZ, int R) {
+#define SPEC_FUSED(lz, r) if (LZ == lz && R == r) return k_fft_real_fused<lz, r>;
+    SPEC_FUSED(512, 8) SPEC_FUSED(512, 16) SPEC_FUSED(1024, 4) SPEC_FUSED(1024, 8)
+#undef SPEC_FUSED
+    return nullptr;
+}
+bool fft_fused_available(int LZ, int R) { return fft_kernel_fused_for(LZ, R) != nullptr; }
 
 // (LZ, R) pairs with a compiled cluster kernel (one trace per cluster of
 // R LZ/8192 CTAs)
@@ -1364,6 +1557,7 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 
 int fft_table_entries(const FftPlan& p) {
     if (p.clustered) return 2 * (cluster_tw4_index(p.H) + fft_twiddle_entries(p.LZ));
+    if (p.fused) return fused_entries(p.LZ, p.R);
     const int generic = p.R * p.T + p.R * p.E + p.H / 2 + 1;
     if (!p.fixed) return generic;
     // + packed pre-twiddles [R/2][LZ] and BlockFFT<LZ> twiddles, float4 each
@@ -1400,6 +1594,27 @@ void fft_fill_table(const FftPlan& p, float2* host) {
             for (int m = 0; m < p.LZ; ++m)
                 pre[(int64_t)g * p.LZ + m] = w((int64_t)(g == 0 ? p.R / 2 : g) * m, H);
         tw4_fill(reinterpret_cast<float4*>(host) + cluster_tw4_index(p.H));
+        return;
+    }
+    if (p.fused) {
+        // pre4: lanes 2g and 2g + 1 at m; BlockFFT twiddles; the unpack bases
+        float4* t4 = reinterpret_cast<float4*>(host);
+        for (int g = 0; g < p.R / 2; ++g)
+            for (int m = 0; m < p.LZ; ++m) {
+                const float2 wa = w((int64_t)(2 * g) * m, H), wb = w((int64_t)(2 * g + 1) * m, H);
+                t4[(int64_t)g * p.LZ + m] = make_float4(wa.x, wb.x, wa.y, wb.y);
+            }
+        tw4_fill(t4 + fused_tw4_index(p.LZ, p.R));
+        const int PT = (p.R / 2) * (p.LZ / 16);
+        const int NS = p.LZ / (1 << (ilog2(p.LZ) % 4));  // span of the fused last pass
+        float4* ub = t4 + fused_ub4_index(p.LZ, p.R);
+        float2* um = host + fused_um_index(p.LZ, p.R);
+        for (int lt = 0; lt < PT; ++lt) {
+            const int r = lt % p.R, q0 = lt / p.R;
+            const float2 wk = w(lt, 2 * H), wq = w(q0, p.LZ);
+            ub[lt] = make_float4(0.5f * wk.x, 0.5f * wk.y, wq.x, wq.y);
+            um[lt] = w(r > 0 ? NS - 1 - q0 : NS - q0, p.LZ);
+        }
         return;
     }
     float2* o = host;
@@ -1450,6 +1665,21 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
         return cudaLaunchKernelEx(&cfg, kc, a);
     }
     const bool dual = p.dual && lanes != 1;
+    if (dual && p.fused) {
+        FftKernel kf = fft_kernel_fused_for(p.LZ, p.R);
+        if (!kf) return cudaErrorInvalidValue;
+        const int PT = (p.R / 2) * (p.LZ / 16);
+        const int F = std::max(1, 256 / PT);
+        const size_t smem = (size_t)F * fused_trace_smem(p.LZ, p.R) * sizeof(float2);
+        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        FftArgs a = {};
+        a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x;
+        a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = 1; a.F = F;
+        a.tab = tab; a.X = X; a.ld_X = ld_X; a.items = items;
+        kf<<<(unsigned)((batch + F - 1) / F), F * PT, smem, st>>>(a);
+        return cudaGetLastError();
+    }
     if (dual && p.fixed) {
         // compile-time (LZ, R): 256 threads, 256 / (R/2 LZ/16) traces per CTA
         FftKernel kf = fft_kernel_fixed_for(p.LZ, p.R);

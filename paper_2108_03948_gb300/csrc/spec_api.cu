@@ -247,11 +247,16 @@ spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, 
     return SPEC_OK;
 }
 
+int table_layout(int kind, const FftPlan& p) {
+    if (kind != 0) return 0;
+    return p.clustered ? 2 : p.fused ? 3 : p.fixed ? 1 : 0;
+}
+
 // Per-shape twiddle tables of the padded real FFT (kind 0) and of the pruned
 // complex FFT (kind 1), built on the host in float64 and cached.
 spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** tab) {
     for (auto& it : c->fft)
-        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax && it.layout == (kind != 0 ? 0 : p.clustered ? 2 : p.fixed ? 1 : 0)) {
+        if (it.kind == kind && it.H == p.H && it.LZ == p.LZ && it.emax == p.emax && it.layout == table_layout(kind, p)) {
             *tab = it.tab;
             return SPEC_OK;
         }
@@ -260,7 +265,7 @@ spec_status plan_table(spec_ctx* c, int kind, const FftPlan& p, const float2** t
     ne.H = p.H;
     ne.LZ = p.LZ;
     ne.emax = p.emax;
-    ne.layout = kind != 0 ? 0 : p.clustered ? 2 : p.fixed ? 1 : 0;
+    ne.layout = table_layout(kind, p);
     std::vector<float2> host((size_t)(kind == 0 ? fft_table_entries(p) : c2c_table_entries(p)));
     if (kind == 0) fft_fill_table(p, host.data());
     else c2c_fill_table(p, host.data());
@@ -444,6 +449,7 @@ spec_status spec_ctx_create(spec_ctx** ctx, int device) {
     c->device = device;
     if (const char* ev = std::getenv("SPEC_LANES")) c->lanes = std::atoi(ev);
     if (const char* ev = std::getenv("SPEC_FFT_CLUSTER")) c->fft_cluster = std::atoi(ev) == 1;
+    if (const char* ev = std::getenv("SPEC_FFT_VARIANT")) c->fft_variant = ev;
     if (const char* ev = std::getenv("SPEC_RAGGED_QUEUE")) c->ragged_queue = std::atoi(ev) == 1 ? 1 : 0;
     c->tune_device = device_tag(device);
     if (const char* ev = std::getenv("SPEC_AUTOTUNE_CACHE")) {
@@ -551,6 +557,42 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     spec_status s = check_common(c, x, batch, n, ld_x, fs, X, bins, ld_X);
     if (s != SPEC_OK) return s;
     if (n_fft < n) return fail(c, SPEC_EINVAL, "n_fft must be >= n (padding never truncates)");
+    MixedPlan mp;
+    std::string why_mixed;
+    if (!is_pow2(n_fft) && mixed_plan(n, n_fft, &mp, &why_mixed)) {
+        // N_FFT with the factors 2, 3, 5, 7 only: the mixed-radix padded FFT
+        if (batch == 0) return SPEC_OK;
+        DeviceGuard g(c->device);
+        cudaStream_t st = (cudaStream_t)stream;
+        if (!is_device_ptr(x) || !is_device_ptr(X))
+            return host_pipeline(c, x, batch, n, ld_x, X, bins, ld_X, st,
+                                 [&](const float* xd, int64_t ld_xd, float2* Xd, int64_t ld_Xd, int64_t nb) {
+                                     return spec_fft(c, xd, nb, n, ld_xd, fs, n_fft, (float*)Xd, ld_Xd, stream);
+                                 });
+        const float2* tab = nullptr;
+        for (auto& it : c->fft)
+            if (it.kind == 4 && it.H == mp.H && it.LZ == mp.LZ) tab = it.tab;
+        if (!tab) {
+            FftEntry ne;
+            ne.kind = 4;
+            ne.H = mp.H;
+            ne.LZ = mp.LZ;
+            std::vector<float2> host((size_t)mp.entries);
+            mixed_fill_table(mp, host.data());
+            cudaError_t e = cudaMalloc(&ne.tab, host.size() * sizeof(float2));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(ne.tab, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                if (ne.tab) cudaFree(ne.tab);
+                return cuda_fail(c, e, "mixed-radix FFT tables");
+            }
+            c->fft.push_back(ne);
+            tab = ne.tab;
+        }
+        cudaError_t e = mixed_launch(mp, x, batch, (int)n, ld_x, tab, reinterpret_cast<float2*>(X), ld_X, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft mixed-radix launch");
+        return SPEC_OK;
+    }
     if (!is_pow2(n_fft)) {
         // any other length: the same bins k fs/N_FFT, k = 0 .. N_FFT/2, as a
         // chirp-z with f1 = 0 and step fs/N_FFT (Eq. 11 on the DFT grid)
@@ -582,10 +624,62 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft multi-pass launch");
         return SPEC_OK;
     }
-    const float2* tab = nullptr;
-    if (p.H > 0 && (s = plan_table(c, 0, p, &tab)) != SPEC_OK) return s;
-    cudaError_t e = fft_launch(p, x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(p.LZ, p.emax), tab,
-                               X2, ld_X, st, c->lanes);
+    // kernel variants of this shape (compiled two-lane, generic two-lane,
+    // one lane, cluster), the fastest chosen by measurement on the first call
+    // (autotune.cu); SPEC_LANES pins the lanes and skips the choice
+    struct Var {
+        FftPlan p;
+        int lanes;
+    };
+    std::vector<Var> vars{{p, c->lanes}};
+    std::vector<std::string> names{p.clustered ? "cluster" : p.fixed ? "fixed" : p.dual ? "dual" : "one"};
+    if (c->lanes == 0 && p.H > 0) {
+        if (p.fixed) {
+            FftPlan q = p;
+            q.fixed = false;
+            vars.push_back({q, 0});
+            names.push_back("dual");
+            if (fft_fused_available(p.LZ, p.R)) {
+                q = p;
+                q.fixed = false;
+                q.fused = true;
+                vars.push_back({q, 0});
+                names.push_back("fused");
+            }
+        }
+        if (p.dual || p.fixed) {
+            vars.push_back({p, 1});
+            names.push_back("one");
+        }
+        FftPlan q;
+        std::string why2;
+        if (!p.clustered && fft_plan(batch, n, n_fft, &q, &why2, true) && q.clustered) {
+            vars.push_back({q, 0});
+            names.push_back("cluster");
+        }
+    }
+    std::vector<const float2*> tabs(vars.size(), nullptr);
+    for (size_t i = 0; i < vars.size(); ++i)
+        if (vars[i].p.H > 0 && (s = plan_table(c, 0, vars[i].p, &tabs[i])) != SPEC_OK) return s;
+    auto run = [&](int i) {
+        const Var& v = vars[(size_t)i];
+        return fft_launch(v.p, x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(v.p.LZ, v.p.emax),
+                          tabs[(size_t)i], X2, ld_X, st, v.lanes);
+    };
+    int pick = 0;
+    int pinned = -1;
+    for (size_t i = 0; i < names.size() && !c->fft_variant.empty(); ++i)
+        if (names[i] == c->fft_variant) pinned = (int)i;
+    if (pinned >= 0) {
+        pick = pinned;
+    } else if (vars.size() > 1) {
+        // keyed by shape only: every batch size (and every chunk of a
+        // host-buffer call) then runs the same arithmetic
+        const std::string key = tune_key("fft", {p.LZ, p.H});
+        pick = tune_pick(c, key, names, run, st, &s);
+        if (pick < 0) return s == SPEC_OK ? fail(c, SPEC_ECUDA, "spec_fft variant timing") : s;
+    }
+    cudaError_t e = run(pick);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft launch");
     return SPEC_OK;
 }
@@ -722,9 +816,19 @@ spec_status spec_czt(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt multi-pass launch");
         return SPEC_OK;
     }
-    cudaError_t e = (czt_dual_ok(L) && c->lanes == 2)
-        ? czt_launch2(en->t, x, batch, ld_x, c->block_tw + block_twiddle_offset(L), X2, ld_X, st)
-        : czt_launch(en->t, x, batch, ld_x, c->block_tw + block_twiddle_offset(L), X2, ld_X, st);
+    // one or two traces per thread (packed lanes): pinned by SPEC_LANES, else
+    // measured on the first call with this shape (autotune.cu)
+    auto run = [&](int i) {
+        return i == 1 ? czt_launch2(en->t, x, batch, ld_x, c->block_tw + block_twiddle_offset(L), X2, ld_X, st)
+                      : czt_launch(en->t, x, batch, ld_x, c->block_tw + block_twiddle_offset(L), X2, ld_X, st);
+    };
+    int pick = (czt_dual_ok(L) && c->lanes == 2) ? 1 : 0;
+    if (c->lanes == 0 && czt_dual_ok(L) && batch >= 2) {
+        const std::string key = tune_key("bluestein", {n, m, L});
+        pick = tune_pick(c, key, {"one", "two"}, run, st, &s);
+        if (pick < 0) return s == SPEC_OK ? fail(c, SPEC_ECUDA, "spec_czt variant timing") : s;
+    }
+    cudaError_t e = run(pick);
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_czt launch");
     return SPEC_OK;
 }
@@ -799,8 +903,19 @@ spec_status spec_zoom(spec_ctx* c, const float* x, int64_t batch, int64_t n, int
         e = zoom_big_launch(p, x, batch, ld_x, taps_d, (float2*)c->stage[3],
                             c->block_tw + block_twiddle_offset(p.fft.LZ), tab, X2, ld_X, st);
     } else {
-        e = zoom_launch(p, x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), X2, ld_X, st,
-                        c->lanes == 2 ? 2 : 1);
+        // one or two traces per CTA: pinned by SPEC_LANES, else measured once
+        auto run = [&](int i) {
+            return zoom_launch(p, x, batch, ld_x, taps_d, c->block_tw + block_twiddle_offset(p.K), X2, ld_X, st,
+                               i == 1 ? 2 : 1);
+        };
+        int pick = c->lanes == 2 ? 1 : 0;
+        if (c->lanes == 0 && p.dual && batch >= 2) {
+            spec_status ts = SPEC_OK;
+            const std::string key = tune_key("zoom", {n, d, n_taps, p.K});
+            pick = tune_pick(c, key, {"one", "two"}, run, st, &ts);
+            if (pick < 0) return ts == SPEC_OK ? fail(c, SPEC_ECUDA, "spec_zoom variant timing") : ts;
+        }
+        e = run(pick);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "spec_zoom launch");
     return SPEC_OK;

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <vector>
 
 namespace spec {
 
@@ -56,6 +57,7 @@ struct FftPlan {
     bool paired = false;  // C > 1 CTAs own residue pairs {r, R - r}: no cluster, local unpack
     bool fixed = false;   // two-lane kernel compiled for this (LZ, R) with packed tables (C == 1)
     bool clustered = false;  // one cluster of C CTAs per trace, conjugate-paired residues (k_fft_real_cluster)
+    bool fused = false;      // fixed two-lane kernel with the last pass fused into the unpack (k_fft_real_fused)
     int emax = 16;      // elements per thread (16 or 32: radix of the passes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
@@ -71,6 +73,8 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 // `fixed` also the packed two-lane pre-twiddles and BlockFFT twiddles),
 // float64 on the host, rounded to float.
 int fft_table_entries(const FftPlan& p);
+// true if k_fft_real_fused has an instance for (LZ, R)
+bool fft_fused_available(int LZ, int R);
 void fft_fill_table(const FftPlan& p, float2* host);
 // lanes: 1 forces one FFT per thread group, otherwise the two-lane kernel is
 // used where the plan allows it.
@@ -94,6 +98,22 @@ int block_twiddle_total();
 int block_twiddle_offset(int LF, int emax = 16);
 void block_twiddle_fill(float2* host);
 int fft_emax_for(int LF);
+
+// ---- mixed-radix padded FFT (k_mixed.cu) -----------------------------------
+// N_FFT even with N_FFT/2 = R LZ, LZ >= ceil(N/2) built from the factors 2, 3,
+// 5 and 7; one CTA per trace with two shared-memory buffers of H values.
+constexpr int kMixedMaxPasses = 16;
+constexpr int64_t kMixedMaxH = 13312;     // 2 H complex values within one CTA's shared memory
+struct MixedPlan {
+    int H = 0, LZ = 0, R = 0;
+    std::vector<int> radix;               // Stockham passes of the LZ-point DFT
+    int pre_off = 0, pass_off = 0, root_off = 0, unpack_off = 0, entries = 0;
+    size_t smem = 0;
+};
+bool mixed_plan(int64_t n, int64_t n_fft, MixedPlan* p, std::string* why);
+void mixed_fill_table(const MixedPlan& p, float2* host);
+cudaError_t mixed_launch(const MixedPlan& p, const float* x, int64_t batch, int n, int64_t ld_x, const float2* tab,
+                         float2* X, int64_t ld_X, cudaStream_t st);
 
 // ---- chirp-z by Bluestein (k_czt.cu) --------------------------------------
 struct CztTables {

@@ -64,6 +64,11 @@ FFT_CASES += [(2, 4000, 32768), (2, 8000, 32768), (2, 2000, 32768), (2, 1500, 65
 # the chirp-z on the DFT grid; the paper's unpadded 500-sample trace among them
 FFT_CASES += [(3, 500, 500), (2, 500, 1000), (2, 2048, 20000), (3, 1000, 12345), (2, 7, 9), (3, 100, 101),
               (2, 20000, 40000)]
+# even lengths whose half has only the factors 2, 3, 5, 7 run the mixed-radix
+# padded FFT (the sweep's 2^k 5^j lengths; radix 3 and 7 passes; R = 1 and a
+# one-point residue DFT)
+FFT_CASES += [(4, 500, 2000), (3, 500, 10000), (2, 500, 20000), (3, 1000, 2000), (2, 2000, 26000),
+              (5, 333, 1050), (3, 12, 42), (2, 1, 6), (3, 4000, 26460)]
 
 
 @pytest.mark.parametrize("batch,n,n_fft", FFT_CASES)
@@ -317,3 +322,34 @@ def test_fft_cluster_kernel_parity(S, monkeypatch):
             got = S.spec_fft(c, dev(x), 20e12, n_fft).cpu().numpy()
             err = rel_rows(got, O.fft_padded(x, n_fft))
             assert err.max() <= TOL, (batch, n, n_fft, err.max())
+
+
+# every (LZ, R) of the fused-unpack kernel (last Stockham pass fused into the
+# unpack): full traces, partial ones (per-sample loads), odd batches (a CTA
+# holding one live trace of two)
+VARIANT_CASES = [(5, 1024, 8192), (3, 1000, 8192), (3, 513, 8192),      # LZ 512, R 8
+                 (3, 1024, 16384), (2, 777, 16384),                      # LZ 512, R 16
+                 (3, 2048, 8192), (3, 1500, 8192),                       # LZ 1024, R 4
+                 (4, 2048, 16384), (3, 1025, 16384)]                     # LZ 1024, R 8
+
+
+@pytest.mark.parametrize("variant", ["fixed", "dual", "fused", "one"])
+def test_fft_kernel_variants_parity(S, monkeypatch, variant):
+    # SPEC_FFT_VARIANT pins the kernel variant the autotuner would otherwise
+    # choose by timing; every variant must meet the same bar
+    monkeypatch.setenv("SPEC_FFT_VARIANT", variant)
+    with S.Context(0) as c:
+        for batch, n, n_fft in VARIANT_CASES:
+            x = traces(batch, n, 7 * n + n_fft)
+            got = S.spec_fft(c, dev(x), 20e12, n_fft).cpu().numpy()
+            err = rel_rows(got, O.fft_padded(x, n_fft))
+            assert err.max() <= TOL, (variant, batch, n, n_fft, err.max())
+        # rows at an odd stride (unaligned starts) into a wider output
+        x = traces(3, 1024, 11)
+        base = torch.zeros((3, 1031), dtype=torch.float32, device="cuda")
+        base[:, :1024] = dev(x)
+        out = torch.full((3, 4200), float("nan"), dtype=torch.complex64, device="cuda")
+        S.spec_fft(c, base, 20e12, 8192, n=1024, out=out)
+        got = out[:, :4097].cpu().numpy()
+        assert rel_rows(got, O.fft_padded(x, 8192)).max() <= TOL
+        assert torch.isnan(out[:, 4097:].real).all()
