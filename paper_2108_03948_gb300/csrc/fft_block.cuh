@@ -361,6 +361,20 @@ template <int P> __host__ __device__ constexpr int pidx_p(int i) { return i + (i
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 __host__ __device__ constexpr bool is_pow2_dev(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Barrier of the threads that share one transform's shared memory: the
+// whole CTA (bar = 0) or the nthr threads (a multiple of 32) of named barrier
+// `bar`, so that transforms sharing a CTA do not wait for one another.
+// (Immediate barrier ids, so that the kernel reserves only the ids it uses.)
+__device__ __forceinline__ void group_sync(int bar, int nthr) {
+    switch (bar) {
+        case 1: asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); break;
+        case 2: asm volatile("bar.sync 2, %0;" ::"r"(nthr) : "memory"); break;
+        case 3: asm volatile("bar.sync 3, %0;" ::"r"(nthr) : "memory"); break;
+        case 4: asm volatile("bar.sync 4, %0;" ::"r"(nthr) : "memory"); break;
+        default: __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- BlockFFT --
 // Radix plan of an LF-point FFT with EMAX (16 or 32) elements per thread:
 // radix-EMAX passes, then one pass of the remaining factor.  Pass p has
@@ -434,11 +448,11 @@ template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typenam
     // Write the outputs of pass P to their Stockham positions, then read the
     // thread's next inputs t + T i.
     template <int P>
-    static __device__ __forceinline__ void exchange(V (&v)[E], SM* s, int t) {
+    static __device__ __forceinline__ void exchange(V (&v)[E], SM* s, int t, int bar = 0, int nthr = 0) {
         constexpr int R = S::radix(P);
         constexpr int NS = S::ns(P);
         constexpr int NB = E / R;
-        __syncthreads();
+        group_sync(bar, nthr);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int j = t + T * b;
@@ -447,7 +461,7 @@ template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typenam
 #pragma unroll
             for (int r = 0; r < R; ++r) sts(s, pidx_p<EMAX>(base + r * NS), v[b + r * NB]);
         }
-        __syncthreads();
+        group_sync(bar, nthr);
 #pragma unroll
         for (int i = 0; i < E; ++i) v[i] = lds(s, pidx_p<EMAX>(t + T * i), (V*)nullptr);
     }
@@ -468,18 +482,21 @@ template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typenam
     // Passes 0 .. NP-1 only (compute and the exchanges between them): the
     // caller fuses the remaining passes into its own data movement.  Thread t
     // then holds the outputs of pass NP-1 that exchange<NP-1> would store.
+    // (bar, nthr): the threads that share `s` synchronise on named barrier
+    // `bar` of nthr threads (bar = 0: the whole CTA)
     template <int P, int NP>
-    static __device__ __forceinline__ void passes_until(V (&v)[E], SM* s, int t, const TW* tw) {
+    static __device__ __forceinline__ void passes_until(V (&v)[E], SM* s, int t, const TW* tw, int bar, int nthr) {
         if constexpr (P < NP) {
-            if constexpr (P > 0) exchange<P - 1>(v, s, t);
+            if constexpr (P > 0) exchange<P - 1>(v, s, t, bar, nthr);
             compute<P>(v, t, tw);
-            passes_until<P + 1, NP>(v, s, t, tw);
+            passes_until<P + 1, NP>(v, s, t, tw, bar, nthr);
         }
     }
     template <int NP>
-    static __device__ __forceinline__ void run_first(V (&v)[E], SM* s, int t, const TW* tw) {
+    static __device__ __forceinline__ void run_first(V (&v)[E], SM* s, int t, const TW* tw, int bar = 0,
+                                                     int nthr = 0) {
         static_assert(NP >= 1 && NP <= S::NPASS, "pass count");
-        passes_until<0, NP>(v, s, t, tw);
+        passes_until<0, NP>(v, s, t, tw, bar, nthr);
     }
 };
 

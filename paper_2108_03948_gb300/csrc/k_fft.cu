@@ -20,6 +20,7 @@
 #include <cstdlib>
 
 #include "fft_block.cuh"
+#include "mbarrier.cuh"
 #include "spec_internal.h"
 
 namespace cg = cooperative_groups;
@@ -38,6 +39,8 @@ struct FftArgs {
     int64_t ld_X;
     const RaggedItem* items;   // ragged batch: per-trace x / X offsets and n (else null)
     int paired;                // C > 1 without a cluster: each CTA owns residue pairs {r, R - r}
+    unsigned* status;          // bounded waits (persistent forms): the context's status word
+    uint64_t timeout_ns;
 };
 
 // Residue of local FFT rl in CTA `rank` of a trace.  Contiguous by default.
@@ -586,15 +589,17 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2r(FftArgs a) {
 // of bank conflicts without padding.
 //
 // Table (float4 units): pre4 [R/2][LZ] = (wa.x, wb.x, wa.y, wb.y),
-// wa = w_H^{2p m}, wb = w_H^{(2p+1) m}; BlockFFT<LZ> twiddles (c, c, s, s);
-// ub4 [PT] = (w_{2H}^{lt}/2, w_LZ^{lt/R}); then (float2 units) um [PT] =
-// w_LZ^{j'(lt)}, the mirror butterfly index of k = lt.  The per-k twiddles
-// are these times compile-time constants (k = lt + PT j: w_{2H}^{PT j} =
-// e^{-j pi j/32}, w_LZ^{(PT/R) j} = e^{-j 2 pi j/32}).
-__host__ __device__ constexpr int fused_tw4_index(int LZ, int R) { return (R / 2) * LZ; }
-__host__ __device__ constexpr int fused_ub4_index(int LZ, int R) { return fused_tw4_index(LZ, R) + fft_twiddle_entries(LZ); }
+// wa = w_H^{2p m}, wb = w_H^{(2p+1) m}; ub4 [PT] = (w_{2H}^{lt}/2,
+// w_LZ^{lt/R}); then (float2 units) um [PT] = w_LZ^{j'(lt)}, the mirror
+// butterfly index of k = lt, and the BlockFFT<LZ> twiddles as (c, s) (8 bytes
+// a twiddle: the float4 (c, c, s, s) form measured 2% slower, the extra L1
+// traffic costing more than the register moves it saves).  The per-k
+// twiddles are ub4 and um times compile-time constants (k = lt + PT j:
+// w_{2H}^{PT j} = e^{-j pi j/32}, w_LZ^{(PT/R) j} = e^{-j 2 pi j/32}).
+__host__ __device__ constexpr int fused_ub4_index(int LZ, int R) { return (R / 2) * LZ; }
 __host__ __device__ constexpr int fused_um_index(int LZ, int R) { return 2 * (fused_ub4_index(LZ, R) + (R / 2) * (LZ / 16)); }
-__host__ __device__ constexpr int fused_entries(int LZ, int R) { return fused_um_index(LZ, R) + (R / 2) * (LZ / 16); }
+__host__ __device__ constexpr int fused_tw2_index(int LZ, int R) { return fused_um_index(LZ, R) + (R / 2) * (LZ / 16); }
+__host__ __device__ constexpr int fused_entries(int LZ, int R) { return fused_tw2_index(LZ, R) + fft_twiddle_entries(LZ); }
 // float2 per trace: the BlockFFT exchange areas of the R/2 pairs (the staged
 // H values fit in the same space)
 __host__ __device__ constexpr int fused_trace_smem(int LZ, int R) { return (R / 2) * padded_len(LZ) * 2; }
@@ -618,67 +623,32 @@ __device__ __forceinline__ void fused_butterfly(float2 (&y)[RHO], float2 w) {
     }
 }
 
+// Passes 0 and 1 of the residue pair's BlockFFT on v (pre-twiddled input
+// m = t + (LZ/16) i), the staging of their outputs and the fused third pass
+// with the unpack into Xr.  Every thread of the CTA calls it (it holds
+// __syncthreads); threads of a trace slot without a trace pass live = false.
 template <int LZ, int R>
-__global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
+__device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl, int t, int lt, bool live,
+                                                 float2* Xr, const float2* tab, int bar, int nthr) {
     using S = FFTShape<LZ, 16>;
     static_assert(S::NPASS == 3 && S::NPB == 2, "fused kernel: radix 16, 16, rho");
     constexpr int RHO = S::REM;
     static_assert(RHO == 2 || RHO == 4, "fused butterflies of radix 2 or 4");
-    constexpr int T = LZ / 16, E = 16, G = R / 2, PT = G * T;
-    constexpr int F = PT >= 256 ? 1 : 256 / PT;
+    constexpr int T = LZ / 16, G = R / 2, PT = G * T;
     constexpr int H = R * LZ;
     constexpr int HB = H / RHO;          // outputs k + n HB share a butterfly
     constexpr int J = 16 / RHO;          // k values per thread
-    constexpr int TS = fused_trace_smem(LZ, R);
     static_assert(PT * J * 2 * RHO == H, "every output once");
     static_assert(PT % 128 == 0 && HB % 128 == 0, "staging swizzle constant along j and m");
     static_assert(PT / R * 32 == LZ, "q steps by LZ/32 along j");
-    using FFT = BlockFFT<LZ, false, C2, 16, float4>;
-    extern __shared__ float4 smem4[];
-
-    const int tid = threadIdx.x;
-    const int f = tid / PT;
-    const int lt = tid - f * PT;
-    const int gl = lt / T;
-    const int t = lt - gl * T;
-    const int64_t b = (int64_t)blockIdx.x * F + f;
-    const bool live = b < a.batch;
-    int n = a.n;
-    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
-    if (a.items && live) {
-        const RaggedItem& it = a.items[b];
-        xo = it.x_off;
-        Xo = it.out_off;
-        n = it.n;
-    }
-    float2* zs = reinterpret_cast<float2*>(smem4) + f * TS;
-    float4* s = reinterpret_cast<float4*>(zs) + gl * padded_len(LZ);
-    const float4* tab4 = reinterpret_cast<const float4*>(a.tab);
-
-    C2 v[E];
-    {
-        const float4* w4 = tab4 + gl * LZ + t;
-        const float* xr = a.x + xo;
-        if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
-            const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
-#pragma unroll
-            for (int i = 0; i < E; ++i) v[i] = pretwiddle2(__ldg(x2 + T * i), __ldg(w4 + T * i));
-        } else {
-#pragma unroll
-            for (int i = 0; i < E; ++i) {
-                const int m = t + T * i;
-                float re = 0.f, im = 0.f;
-                if (live && 2 * m < n) re = __ldg(xr + 2 * m);
-                if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
-                v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
-            }
-        }
-    }
-    FFT::template run_first<2>(v, s, t, tab4 + fused_tw4_index(LZ, R));
+    const float4* tab4 = reinterpret_cast<const float4*>(tab);
+    using FFT = BlockFFT<LZ, false, C2, 16, float2>;
+    FFT::template run_first<2>(v, reinterpret_cast<float4*>(zs) + gl * padded_len(LZ), t,
+                               tab + fused_tw2_index(LZ, R), bar, nthr);
 
     // outputs of pass 1 (radix 16, span 16): v[r] is position base + 16 r of
     // residues 2 gl and 2 gl + 1, staged at x = pos R + 2 gl
-    __syncthreads();
+    group_sync(bar, nthr);
     {
         const int k16 = t & 15;
         const int pos0 = (t - k16) * 16 + k16;
@@ -689,14 +659,13 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
             st4[fsw(x) >> 1] = make_float4(v[r].re.x, v[r].im.x, v[r].re.y, v[r].im.y);
         }
     }
-    __syncthreads();
+    group_sync(bar, nthr);
     if (!live) return;
 
-    float2* Xr = a.X + Xo;
     const float4 ub = __ldg(tab4 + fused_ub4_index(LZ, R) + lt);
     const float2 wk0 = make_float2(ub.x, ub.y);    // w_{2H}^{lt} / 2
     const float2 wq0 = make_float2(ub.z, ub.w);    // w_LZ^{lt/R}
-    const float2 wm0 = __ldg(a.tab + fused_um_index(LZ, R) + lt);
+    const float2 wm0 = __ldg(tab + fused_um_index(LZ, R) + lt);
     // the swizzle depends only on the low 7 bits of x, and PT j, m HB are
     // multiples of 128: every slot below is a base plus a constant
     const float2* zf = zs + fsw(lt);
@@ -741,6 +710,128 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
         // pairs (HB/2 + n HB, H - HB/2 - n HB), twiddle e^{-j pi (2n+1)/(2 rho)}/2
         unpack_pair_half<H>(Xr, HB / 2, A[0], A[RHO - 1], cscale(wpi32(16 / RHO), 0.5f));
         if constexpr (RHO == 4) unpack_pair_half<H>(Xr, HB / 2 + HB, A[1], A[2], cscale(wpi32(48 / RHO), 0.5f));
+    }
+}
+
+template <int LZ, int R>
+__global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
+    constexpr int T = LZ / 16, E = 16, G = R / 2, PT = G * T;
+    constexpr int F = PT >= 256 ? 1 : 256 / PT;
+    constexpr int TS = fused_trace_smem(LZ, R);
+    extern __shared__ float4 smem4[];
+
+    const int tid = threadIdx.x;
+    const int f = tid / PT;
+    const int lt = tid - f * PT;
+    const int gl = lt / T;
+    const int t = lt - gl * T;
+    const int64_t b = (int64_t)blockIdx.x * F + f;
+    const bool live = b < a.batch;
+    int n = a.n;
+    int64_t xo = (live ? b : 0) * a.ld_x, Xo = (live ? b : 0) * a.ld_X;
+    if (a.items && live) {
+        const RaggedItem& it = a.items[b];
+        xo = it.x_off;
+        Xo = it.out_off;
+        n = it.n;
+    }
+    const float4* w4 = reinterpret_cast<const float4*>(a.tab) + gl * LZ + t;
+    C2 v[E];
+    const float* xr = a.x + xo;
+    if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
+        const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = pretwiddle2(__ldg(x2 + T * i), __ldg(w4 + T * i));
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            float re = 0.f, im = 0.f;
+            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+            v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
+        }
+    }
+    // F > 1: each trace's threads synchronise on their own named barrier
+    fused_fft_unpack<LZ, R>(v, reinterpret_cast<float2*>(smem4) + f * TS, gl, t, lt, live, a.X + Xo, a.tab,
+                            F > 1 ? 1 + f : 0, PT);
+}
+
+// Persistent form for whole rows at 16-byte aligned addresses (n = 2 LZ,
+// 16-byte row pitch, no ragged items): two CTAs per SM loop over groups of F
+// traces, and while a group is transformed one thread has the next group's
+// rows copied into shared memory by the bulk-copy engine (cp.async.bulk,
+// completion counted on an mbarrier per buffer), so that no warp waits on
+// HBM latency for its input.  Every wait is bounded: one that gives up sets
+// the context's status word, and the CTA leaves at the next group boundary
+// after waiting (bounded) for the copies it still has in flight.
+__host__ __device__ constexpr size_t fused_tma_smem(int LZ, int R) {
+    return ((size_t)(256 / ((R / 2) * (LZ / 16)) > 1 ? 256 / ((R / 2) * (LZ / 16)) : 1)) *
+               ((size_t)fused_trace_smem(LZ, R) * sizeof(float2) + 2 * (size_t)(2 * LZ) * sizeof(float)) + 16;
+}
+
+template <int LZ, int R>
+__global__ void __launch_bounds__(256, 2) k_fft_real_fused_tma(FftArgs a) {
+    constexpr int T = LZ / 16, E = 16, G = R / 2, PT = G * T;
+    constexpr int F = PT >= 256 ? 1 : 256 / PT;
+    constexpr int TS = fused_trace_smem(LZ, R);
+    constexpr int XB = 2 * LZ;                       // floats of one row
+    extern __shared__ float4 smem4[];
+    float2* zs_all = reinterpret_cast<float2*>(smem4);
+    float* xbuf = reinterpret_cast<float*>(zs_all + F * TS);        // [2][F][XB]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(xbuf + 2 * F * XB);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int f = tid / PT;
+    const int lt = tid - f * PT;
+    const int gl = lt / T;
+    const int t = lt - gl * T;
+    const int64_t groups = (a.batch + F - 1) / F;
+    const Guard guard{&abort_flag, a.status, a.timeout_ns};
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // thread 0: copies issued per buffer (the parity of a use is its count mod 2)
+    uint32_t issued0 = 0, issued1 = 0;
+    auto issue = [&](int64_t g, int buf) {
+        const int nl = (int)(a.batch - g * F < F ? a.batch - g * F : F);
+        mbar_expect_tx(bars + buf, (uint32_t)(nl * XB * sizeof(float)));
+        for (int q = 0; q < nl; ++q)
+            bulk_load(xbuf + (buf * F + q) * XB, a.x + (g * F + q) * a.ld_x, (uint32_t)(XB * sizeof(float)), bars + buf);
+        if (buf) ++issued1;
+        else ++issued0;
+    };
+    int64_t g = blockIdx.x;
+    if (tid == 0 && g < groups) issue(g, 0);
+    const float4* w4 = reinterpret_cast<const float4*>(a.tab) + gl * LZ + t;
+    for (int it = 0; g < groups; ++it, g += gridDim.x) {
+        const int buf = it & 1;
+        __syncthreads();            // the last group's reads of zs and of xbuf[buf ^ 1] are done
+        if (abort_flag) break;
+        if (tid == 0 && g + gridDim.x < groups) issue(g + gridDim.x, buf ^ 1);
+        wait_bounded(bars + buf, (uint32_t)((it >> 1) & 1), guard);
+        const int64_t b = g * F + f;
+        const bool live = b < a.batch;
+        const float2* x2 = reinterpret_cast<const float2*>(xbuf + (buf * F + f) * XB) + t;
+        C2 v[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = pretwiddle2(live ? x2[T * i] : make_float2(0.f, 0.f), __ldg(w4 + T * i));
+        fused_fft_unpack<LZ, R>(v, zs_all + f * TS, gl, t, lt, live, a.X + (live ? b : 0) * a.ld_X, a.tab, 0, 0);
+    }
+    // after an abort: no copy may still be writing into this CTA's memory
+    if (tid == 0 && abort_flag) {
+        for (int q = 0; q < 2; ++q) {
+            const uint32_t n_is = q ? issued1 : issued0;
+            if (n_is == 0) continue;
+            const uint64_t t0 = gtime();
+            while (!mbar_try_wait(bars + q, (n_is - 1) & 1) && gtime() - t0 < a.timeout_ns) {
+            }
+        }
     }
 }
 
@@ -1425,8 +1516,8 @@ static FftKernel fft_kernel_fixed_for(int LZ, int R) {
 
 // (LZ, R) pairs with a compiled fused-unpack kernel (three-pass BlockFFT,
 // R/2 LZ/16 threads per trace a multiple of 128)
-static FftKernel fft_kernel_fused_for(int LZ, int R) {
-#define SPEC_FUSED(lz, r) if (LZ == lz && R == r) return k_fft_real_fused<lz, r>;
+static FftKernel fft_kernel_fused_for(int LZ, int R, bool tma = false) {
+#define SPEC_FUSED(lz, r) if (LZ == lz && R == r) return tma ? k_fft_real_fused_tma<lz, r> : k_fft_real_fused<lz, r>;
     SPEC_FUSED(512, 8) SPEC_FUSED(512, 16) SPEC_FUSED(1024, 4) SPEC_FUSED(1024, 8)
 #undef SPEC_FUSED
     return nullptr;
@@ -1604,7 +1695,13 @@ void fft_fill_table(const FftPlan& p, float2* host) {
                 const float2 wa = w((int64_t)(2 * g) * m, H), wb = w((int64_t)(2 * g + 1) * m, H);
                 t4[(int64_t)g * p.LZ + m] = make_float4(wa.x, wb.x, wa.y, wb.y);
             }
-        tw4_fill(t4 + fused_tw4_index(p.LZ, p.R));
+        {
+            // BlockFFT<LZ> twiddles as (c, s): the packed form, then repacked
+            std::vector<float4> t4tw((size_t)fft_twiddle_entries(p.LZ));
+            tw4_fill(t4tw.data());
+            float2* d2 = host + fused_tw2_index(p.LZ, p.R);
+            for (size_t e = 0; e < t4tw.size(); ++e) d2[e] = make_float2(t4tw[e].x, t4tw[e].z);
+        }
         const int PT = (p.R / 2) * (p.LZ / 16);
         const int NS = p.LZ / (1 << (ilog2(p.LZ) % 4));  // span of the fused last pass
         float4* ub = t4 + fused_ub4_index(p.LZ, p.R);
@@ -1632,6 +1729,34 @@ void fft_fill_table(const FftPlan& p, float2* host) {
             *o4++ = make_float4(wa.x, wb.x, wa.y, wb.y);
         }
     tw4_fill(reinterpret_cast<float4*>(host) + fixed_tw4_index(p.LZ, p.R));
+}
+
+bool fft_fused_tma_ok(const FftPlan& p, const float* x, int n, int64_t ld_x) {
+    return p.fused && fft_kernel_fused_for(p.LZ, p.R, true) != nullptr && n == 2 * p.LZ &&
+           (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ld_x & 3) == 0;
+}
+
+cudaError_t fft_fused_tma_launch(const FftPlan& p, const float* x, int64_t batch, int64_t ld_x, const float2* tab,
+                                 float2* X, int64_t ld_X, unsigned* status, uint64_t timeout_ns, int sms,
+                                 cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    FftKernel kf = fft_kernel_fused_for(p.LZ, p.R, true);
+    if (!kf) return cudaErrorInvalidValue;
+    const int PT = (p.R / 2) * (p.LZ / 16);
+    const int F = std::max(1, 256 / PT);
+    const size_t smem = fused_tma_smem(p.LZ, p.R);
+    cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    FftArgs a = {};
+    a.x = x; a.batch = batch; a.n = 2 * p.LZ; a.ld_x = ld_x;
+    a.H = p.H; a.logR = ilog2(p.R); a.Rc = p.Rc; a.C = 1; a.F = F;
+    a.tab = tab; a.X = X; a.ld_X = ld_X;
+    a.status = status;
+    a.timeout_ns = timeout_ns;
+    const int64_t groups = (batch + F - 1) / F;
+    const int64_t grid = std::min<int64_t>(groups, 2 * (int64_t)std::max(1, sms));
+    kf<<<(unsigned)grid, F * PT, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,

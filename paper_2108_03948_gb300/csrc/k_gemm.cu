@@ -32,6 +32,7 @@
 
 #include <mutex>
 
+#include "mbarrier.cuh"
 #include "spec_internal.h"
 
 namespace spec {
@@ -52,55 +53,6 @@ constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t
 // The same with A and B BF16 (format 1 at bits 7-9 and 10-12; both operands
 // always share one format)
 constexpr uint32_t kIdescBf16 = kIdesc | (1u << 7) | (1u << 10);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtime() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-struct Guard {
-    volatile int* abort;       // shared: set by the first wait that gives up
-    unsigned* status;          // global: the context's status word
-    uint64_t timeout_ns;
-};
-
-// Wait for the phase of `bar` with parity `parity`, at most timeout_ns; on
-// a timeout flag the CTA and the context.  Returns false if the CTA aborts.
-__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, const Guard& g) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = gtime();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*g.abort) return false;
-        if (gtime() - t0 > g.timeout_ns) {
-            *g.abort = 1;
-            atomicOr(g.status, 1u);
-            return false;
-        }
-    }
-    return true;
-}
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
@@ -187,7 +139,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mbar_init(done, 1);
         *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -539,7 +491,7 @@ __global__ void k_wait_selftest(unsigned* status, uint64_t timeout_ns) {
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     __syncthreads();
     const Guard g{&abort_flag, status, timeout_ns};

@@ -645,6 +645,11 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
                 q.fused = true;
                 vars.push_back({q, 0});
                 names.push_back("fused");
+
+                if (fft_fused_tma_ok(q, x, (int)n, ld_x)) {
+                    vars.push_back({q, 4});
+                    names.push_back("fusedp");
+                }
             }
         }
         if (p.dual || p.fixed) {
@@ -663,6 +668,9 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
         if (vars[i].p.H > 0 && (s = plan_table(c, 0, vars[i].p, &tabs[i])) != SPEC_OK) return s;
     auto run = [&](int i) {
         const Var& v = vars[(size_t)i];
+        if (v.lanes == 4)      // the persistent fused kernel (bulk-copy prefetch, bounded waits)
+            return fft_fused_tma_launch(v.p, x, batch, ld_x, tabs[(size_t)i], X2, ld_X, c->status,
+                                        c->wait_timeout_ns, c->sms, st);
         return fft_launch(v.p, x, batch, (int)n, ld_x, c->block_tw + block_twiddle_offset(v.p.LZ, v.p.emax),
                           tabs[(size_t)i], X2, ld_X, st, v.lanes);
     };

@@ -75,6 +75,12 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 int fft_table_entries(const FftPlan& p);
 // true if k_fft_real_fused has an instance for (LZ, R)
 bool fft_fused_available(int LZ, int R);
+// The persistent fused kernel that prefetches rows with bulk copies: whole
+// rows (n = 2 LZ) at 16-byte aligned addresses and pitch only.
+bool fft_fused_tma_ok(const FftPlan& p, const float* x, int n, int64_t ld_x);
+cudaError_t fft_fused_tma_launch(const FftPlan& p, const float* x, int64_t batch, int64_t ld_x, const float2* tab,
+                                 float2* X, int64_t ld_X, unsigned* status, uint64_t timeout_ns, int sms,
+                                 cudaStream_t st);
 void fft_fill_table(const FftPlan& p, float2* host);
 // lanes: 1 forces one FFT per thread group, otherwise the two-lane kernel is
 // used where the plan allows it.

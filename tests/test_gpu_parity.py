@@ -333,7 +333,7 @@ VARIANT_CASES = [(5, 1024, 8192), (3, 1000, 8192), (3, 513, 8192),      # LZ 512
                  (4, 2048, 16384), (3, 1025, 16384)]                     # LZ 1024, R 8
 
 
-@pytest.mark.parametrize("variant", ["fixed", "dual", "fused", "one"])
+@pytest.mark.parametrize("variant", ["fixed", "dual", "fused", "fusedp", "one"])
 def test_fft_kernel_variants_parity(S, monkeypatch, variant):
     # SPEC_FFT_VARIANT pins the kernel variant the autotuner would otherwise
     # choose by timing; every variant must meet the same bar
