@@ -362,15 +362,20 @@ __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c
 __host__ __device__ constexpr bool is_pow2_dev(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // Barrier of the threads that share one transform's shared memory: the
-// whole CTA (bar = 0) or the nthr threads (a multiple of 32) of named barrier
-// `bar`, so that transforms sharing a CTA do not wait for one another.
-// (Immediate barrier ids, so that the kernel reserves only the ids it uses.)
+// whole CTA (bar = 0), the calling warp alone (bar = -1), or the nthr threads
+// (a multiple of 32) of named barrier `bar` (1 .. 7), so that transforms
+// sharing a CTA do not wait for one another.  (Immediate barrier ids, so that
+// the kernel reserves only the ids it uses.)
 __device__ __forceinline__ void group_sync(int bar, int nthr) {
     switch (bar) {
+        case -1: __syncwarp(); break;
         case 1: asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); break;
         case 2: asm volatile("bar.sync 2, %0;" ::"r"(nthr) : "memory"); break;
         case 3: asm volatile("bar.sync 3, %0;" ::"r"(nthr) : "memory"); break;
         case 4: asm volatile("bar.sync 4, %0;" ::"r"(nthr) : "memory"); break;
+        case 5: asm volatile("bar.sync 5, %0;" ::"r"(nthr) : "memory"); break;
+        case 6: asm volatile("bar.sync 6, %0;" ::"r"(nthr) : "memory"); break;
+        case 7: asm volatile("bar.sync 7, %0;" ::"r"(nthr) : "memory"); break;
         default: __syncthreads();
     }
 }

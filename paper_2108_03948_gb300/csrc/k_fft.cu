@@ -627,9 +627,11 @@ __device__ __forceinline__ void fused_butterfly(float2 (&y)[RHO], float2 w) {
 // m = t + (LZ/16) i), the staging of their outputs and the fused third pass
 // with the unpack into Xr.  Every thread of the CTA calls it (it holds
 // __syncthreads); threads of a trace slot without a trace pass live = false.
+// (bar, nthr): the trace's barrier (group_sync); pbar: the barrier of the
+// residue pair's exchange (-1: the pair is one warp), 64 threads.
 template <int LZ, int R>
 __device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl, int t, int lt, bool live,
-                                                 float2* Xr, const float2* tab, int bar, int nthr) {
+                                                 float2* Xr, const float2* tab, int bar, int nthr, int pbar) {
     using S = FFTShape<LZ, 16>;
     static_assert(S::NPASS == 3 && S::NPB == 2, "fused kernel: radix 16, 16, rho");
     constexpr int RHO = S::REM;
@@ -643,8 +645,9 @@ __device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl
     static_assert(PT / R * 32 == LZ, "q steps by LZ/32 along j");
     const float4* tab4 = reinterpret_cast<const float4*>(tab);
     using FFT = BlockFFT<LZ, false, C2, 16, float2>;
+    // the exchange between passes 0 and 1 touches only the pair's own area
     FFT::template run_first<2>(v, reinterpret_cast<float4*>(zs) + gl * padded_len(LZ), t,
-                               tab + fused_tw2_index(LZ, R), bar, nthr);
+                               tab + fused_tw2_index(LZ, R), pbar, T);
 
     // outputs of pass 1 (radix 16, span 16): v[r] is position base + 16 r of
     // residues 2 gl and 2 gl + 1, staged at x = pos R + 2 gl
@@ -752,9 +755,12 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
             v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
         }
     }
-    // F > 1: each trace's threads synchronise on their own named barrier
+    // F > 1: each trace's threads synchronise on their own named barrier;
+    // each residue pair's exchange on its warp (T = 32) or on a named
+    // barrier of its two warps (ids after the traces')
+    static_assert(T == 32 || (T == 64 && F + F * G < 8), "barrier ids");
     fused_fft_unpack<LZ, R>(v, reinterpret_cast<float2*>(smem4) + f * TS, gl, t, lt, live, a.X + Xo, a.tab,
-                            F > 1 ? 1 + f : 0, PT);
+                            F > 1 ? 1 + f : 0, PT, T == 32 ? -1 : 1 + F + f * G + gl);
 }
 
 // Persistent form for whole rows at 16-byte aligned addresses (n = 2 LZ,
@@ -821,7 +827,7 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_fused_tma(FftArgs a) {
         C2 v[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) v[i] = pretwiddle2(live ? x2[T * i] : make_float2(0.f, 0.f), __ldg(w4 + T * i));
-        fused_fft_unpack<LZ, R>(v, zs_all + f * TS, gl, t, lt, live, a.X + (live ? b : 0) * a.ld_X, a.tab, 0, 0);
+        fused_fft_unpack<LZ, R>(v, zs_all + f * TS, gl, t, lt, live, a.X + (live ? b : 0) * a.ld_X, a.tab, 0, 0, 0);
     }
     // after an abort: no copy may still be writing into this CTA's memory
     if (tid == 0 && abort_flag) {
