@@ -153,16 +153,25 @@ def host_link_gbs(dev, nbytes=256 << 20, reps=5):
     return {"h2d_gbs": timed(True, False), "d2h_gbs": timed(False, True), "duplex_gbs": timed(True, True)}
 
 
-def csrc_digest():
-    """Digest of the kernel sources: stored traffic counters are valid only
-    for the sources they were taken from."""
+# Kernel sources behind each transform's timed launches: stored traffic
+# counters stay valid while these files are unchanged.
+DIGEST_SOURCES = {
+    "fft": ["k_fft.cu", "k_long.cu", "fft_block.cuh", "mbarrier.cuh", "spec_internal.h"],
+    "czt": ["k_czt.cu", "k_gemm.cu", "k_long.cu", "fft_block.cuh", "mbarrier.cuh", "spec_internal.h"],
+    "zoom": ["k_zoom.cu", "k_fft.cu", "fft_block.cuh", "spec_internal.h"],
+}
+
+
+def csrc_digest(kernel, workload=None):
+    """Digest of the kernel sources of one transform (plus the ragged plan for
+    workload 2): stored traffic counters are valid only for those sources."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2108_03948_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    names = list(DIGEST_SOURCES[kernel]) + (["ragged.cu"] if workload == 2 else [])
+    for name in sorted(names):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -175,7 +184,7 @@ def traffic_for(workload, kernel):
     with open(p) as f:
         d = json.load(f)
     e = d.get(f"workload_{workload}", {}).get(kernel)
-    if not e or e.get("csrc_digest") != csrc_digest():
+    if not e or e.get("csrc_digest") != csrc_digest(kernel, workload):
         return None
     return e.get("per_launch_bytes")
 
