@@ -500,7 +500,7 @@ template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typenam
     template <int NP>
     static __device__ __forceinline__ void run_first(V (&v)[E], SM* s, int t, const TW* tw, int bar = 0,
                                                      int nthr = 0) {
-        static_assert(NP >= 1 && NP <= S::NPASS, "pass count");
+        static_assert(NP >= 0 && NP <= S::NPASS, "pass count");
         passes_until<0, NP>(v, s, t, tw, bar, nthr);
     }
 };

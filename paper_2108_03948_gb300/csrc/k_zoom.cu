@@ -163,35 +163,78 @@ __global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 1024 ? 1 : (
     }
 }
 
+// The blocked FIR of zoom_fir_blocked on two traces side by side: xs holds
+// (trace 2p, trace 2p+1) sample pairs, taps are stored (g.re, g.re, g.im,
+// g.im), and every accumulator is a packed pair.  The window reads of a warp
+// (float2 at stride B = 3) and its staging stores fall on distinct banks.
+template <int B, int T>
+__device__ __forceinline__ void zoom_fir_blocked2(const float4* tap, const float2* xs, float4* s, int n_taps,
+                                                  int lout, int rs, uint64_t Cn, int D, int t) {
+    const int J = n_taps - 1;
+    for (int m0 = B * t; m0 < lout; m0 += B * T) {
+        float2 re[B], im[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) re[u] = im[u] = make_float2(0.f, 0.f);
+        for (int p = 0; p < D && p <= J; ++p) {
+            const float2* row = xs + p * rs + m0;
+            const float4* tp = tap + (J - p);                // tap of step c: tp[-D c]
+            const int np = (J - p) / D + 1;
+            float2 w[B];
+#pragma unroll
+            for (int u = 0; u + 1 < B; ++u) w[u + 1] = row[u];
+#pragma unroll 3
+            for (int c = 0; c < np; ++c) {
+#pragma unroll
+                for (int u = 0; u + 1 < B; ++u) w[u] = w[u + 1];
+                w[B - 1] = row[c + B - 1];                   // window: w[u] = row[c + u]
+                const float4 g = tp[-D * c];
+                const float2 gr = make_float2(g.x, g.y), gi = make_float2(g.z, g.w);
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    re[u] = fma2(gr, w[u], re[u]);
+                    im[u] = fma2(gi, w[u], im[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int m = m0 + u;
+            if (m < lout) {
+                const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
+                sts(s, pidx(m), mul_tw<false>(C2{re[u], im[u]}, rot));
+            }
+        }
+    }
+}
+
 // Two-lane variant: traces 2p and 2p+1 share one CTA.  Their samples sit
 // side by side in shared memory (one float2 per polyphase slot), so each tap
 // -- stored duplicated as (g.re, g.re, g.im, g.im) -- feeds both traces with
 // two packed multiply-adds, and the FFT runs on packed pairs.
 template <int K>
-__global__ void __launch_bounds__(FFTShape<K>::T) k_zoom2(ZoomArgs a) {
+__global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 512 ? 1 : FFTShape<K>::T >= 128 ? 512 / FFTShape<K>::T : 4)
+    k_zoom2(ZoomArgs a) {
     using FFT = BlockFFT<K, false, C2>;
     constexpr int E = FFT::E, T = FFT::T;
     extern __shared__ float4 smem4[];
     const int t = threadIdx.x;
     const int64_t b0 = 2 * (int64_t)blockIdx.x, b1 = b0 + 1;
     const bool live1 = b1 < a.batch;
-    const int J = a.n_taps - 1;
     const int D = a.d;
 
     // shared layout: taps (g.re, g.re, g.im, g.im) | polyphase x pairs |
-    // FFT exchange (float4) | tap offsets (int) | slack
+    // FFT exchange (float4) | slack (a window that runs past L_out reads into
+    // the FFT area; its results are discarded)
     float4* tap = smem4;
     float2* xs = reinterpret_cast<float2*>(smem4 + a.n_taps);
     float4* s = smem4 + a.n_taps + (D * a.rs + 1) / 2;
-    int* toff = reinterpret_cast<int*>(s + padded_len(K));
 
     for (int k = t; k < a.n_taps; k += T) {
         const float h = __ldg(a.taps + k);
         const float2 e = unit_fixed(a.Cn * (uint64_t)k, false);
-        const int q = J - k;
         tap[k] = make_float4(h * e.x, h * e.x, h * e.y, h * e.y);
-        toff[k] = (q % D) * a.rs + q / D;
     }
+    const int J = a.n_taps - 1;
     const float* x0 = a.x + b0 * a.ld_x;
     const float* x1 = a.x + (live1 ? b1 : b0) * a.ld_x;
     const int total = D * a.rs;
@@ -204,31 +247,10 @@ __global__ void __launch_bounds__(FFTShape<K>::T) k_zoom2(ZoomArgs a) {
     }
     __syncthreads();
 
-    for (int m0 = t; m0 < a.lout; m0 += kZoomGroup * T) {
-        float2 re[kZoomGroup], im[kZoomGroup];
-#pragma unroll
-        for (int u = 0; u < kZoomGroup; ++u) re[u] = im[u] = make_float2(0.f, 0.f);
-        const float2* xm = xs + m0;
-        for (int k = 0; k < a.n_taps; ++k) {
-            const float4 g = tap[k];
-            const float2* xk = xm + toff[k];
-            const float2 gr = make_float2(g.x, g.y), gi = make_float2(g.z, g.w);
-#pragma unroll
-            for (int u = 0; u < kZoomGroup; ++u) {
-                const float2 xv = xk[u * T];
-                re[u] = fma2(gr, xv, re[u]);
-                im[u] = fma2(gi, xv, im[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kZoomGroup; ++u) {
-            const int m = m0 + u * T;
-            if (m < a.lout) {
-                const float2 rot = unit_fixed(a.Cn * ((uint64_t)m * (uint64_t)D), true);
-                sts(s, pidx(m), mul_tw<false>(C2{re[u], im[u]}, rot));
-            }
-        }
-    }
+    // FIR + decimate for both traces at once: the blocked sliding window of
+    // zoom_fir_blocked with packed (trace 2p, trace 2p+1) samples, so each
+    // tap read feeds 2 B outputs with B packed multiply-adds per component
+    zoom_fir_blocked2<3, T>(tap, xs, s, a.n_taps, a.lout, a.rs, a.Cn, D, t);
     __syncthreads();
     C2 v[E];
 #pragma unroll
@@ -434,9 +456,9 @@ bool zoom_plan(int64_t n, int64_t d, int64_t n_taps, int64_t n_fft, double fs, d
     }
     p->n = (int)n; p->d = (int)d; p->n_taps = (int)n_taps; p->K = (int)K; p->lout = (int)lout;
     p->rs = (int)rs;
-    // two-lane layout: taps (16 B) + polyphase pairs + float4 FFT area + offsets + slack
+    // two-lane layout: taps (16 B) + polyphase pairs + float4 FFT area + slack
     p->smem2 = (size_t)n_taps * 16 + (size_t)((d * rs + 1) / 2) * 16 + (size_t)padded_len((int)K) * 16 +
-               (size_t)n_taps * 4 + (size_t)kZoomGroup * T * 8;
+               (size_t)kZoomGroup * T * 8;
     p->dual = K >= 16 && K <= 8192 && p->smem2 <= 200 * 1024;
     p->Cn = cycles_to_fixed(0.5 * (f1 + f2) / fs);
     p->threads = T;

@@ -353,3 +353,24 @@ def test_fft_kernel_variants_parity(S, monkeypatch, variant):
         got = out[:, :4097].cpu().numpy()
         assert rel_rows(got, O.fft_padded(x, 8192)).max() <= TOL
         assert torch.isnan(out[:, 4097:].real).all()
+
+
+@pytest.mark.parametrize("lanes", ["1", "2"])
+def test_zoom_and_bluestein_lane_forms_parity(S, monkeypatch, lanes):
+    # SPEC_LANES pins one trace per thread group (1) or two packed traces (2)
+    # for the Bluestein and Zoom kernels, which the autotuner otherwise picks
+    # by timing; both forms meet the same bar, odd batches included
+    monkeypatch.setenv("SPEC_LANES", lanes)
+    fs = 20e12
+    with S.Context(0) as c:
+        for batch, n, f1, f2, d, nt, n_fft in ZOOM_CASES[:9]:
+            x = traces(batch, n, 300 + n + d)
+            h = O.design_lowpass(nt, d).astype(np.float32)
+            got = S.spec_zoom(c, dev(x), fs, f1, f2, d, dev(h), n_fft).cpu().numpy()
+            err = rel_rows(got, O.zoom(x, fs, f1, f2, d, h, n_fft))
+            assert err.max() <= TOL, (lanes, batch, n, d, nt, n_fft, err.max())
+        for batch, n, f1, f2, m in CZT_CASES:
+            x = traces(batch, n, 200 + n + m)
+            got = S.spec_czt(c, dev(x), fs, f1, f2, m, mode=S.SPEC_CZT_BLUESTEIN).cpu().numpy()
+            err = rel_rows(got, O.czt(x, fs, f1, f2, m))
+            assert err.max() <= TOL, (lanes, batch, n, m, err.max())
