@@ -73,21 +73,22 @@ template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
 }
 
 // e^{sign j 2 pi ph/2^64}: `ph` is a phase in cycles as a 64-bit fixed-point
-// fraction.  The top bits go through sincospif; the remainder (below 2^-24
-// of a half-cycle) is applied to first order, so the result is accurate to
-// about 1e-8 absolute whatever the size of the original phase.
+// fraction.  Its top 24 bits q (a signed cycle fraction q 2^-24, exact in
+// float) go through sincospif; the remainder r = ph - q 2^40, below 2^40
+// (an angle under 2 pi 2^-24), is applied to first order (the neglected
+// second-order term is below 1e-13), so the result is accurate to the float
+// rounding of cos and sin (below 1e-7 absolute) whatever the size of the
+// original phase.  Only 32-bit integer to
+// float conversions are used: the 64-bit ones run on the (slow) FP64 pipe.
 __device__ __forceinline__ float2 unit_fixed(uint64_t ph, bool negative) {
-    const int64_t s = (int64_t)ph;                     // cycles in [-1/2, 1/2) * 2^64
-    const int32_t hi = (int32_t)(s >> 32);
-    const float hf = (float)hi;                        // rounded to 24 bits
-    // small remainder; unsigned arithmetic, because hf may round up to 2^31
-    const int64_t rem = (int64_t)((uint64_t)s - ((uint64_t)(int64_t)hf << 32));
-    const float xf = hf * 4.656612873077393e-10f;      // * 2^-31 (half-cycles)
-    const float xr = (float)rem * 1.0842021724855044e-19f * 3.14159265358979f;  // * 2^-63 * pi
+    const int32_t q = (int32_t)((int64_t)ph >> 40);            // [-2^23, 2^23)
+    const uint64_t r = ph - ((uint64_t)(int64_t)q << 40);       // [0, 2^40)
+    const float xf = (float)q * 1.1920928955078125e-07f;       // * 2^-23 (half-cycles)
+    const float xr = (float)(int32_t)(r >> 9) * 1.7439342e-16f;  // * 2^9 2^-64 2 pi (radians)
     float sn, cs;
     sincospif(xf, &sn, &cs);
-    float re = fmaf(-xr, sn, cs);
-    float im = fmaf(xr, cs, sn);
+    const float re = fmaf(-xr, sn, cs);
+    const float im = fmaf(xr, cs, sn);
     return negative ? make_float2(re, -im) : make_float2(re, im);
 }
 
@@ -96,12 +97,10 @@ __device__ __forceinline__ float2 unit_fixed(uint64_t ph, bool negative) {
 // guarantees), with the same first-order remainder: for chirps evaluated in a
 // kernel, where the library call's cost matters.
 __device__ __forceinline__ float2 unit_fast(uint64_t ph, bool negative) {
-    const int64_t s = (int64_t)ph;
-    const int32_t hi = (int32_t)(s >> 32);
-    const float hf = (float)hi;
-    const int64_t rem = (int64_t)((uint64_t)s - ((uint64_t)(int64_t)hf << 32));
-    const float ang = hf * 1.4629180792671596e-9f;                      // * 2 pi / 2^32
-    const float xr = (float)rem * 1.0842021724855044e-19f * 3.14159265358979f;
+    const int32_t q = (int32_t)((int64_t)ph >> 40);
+    const uint64_t r = ph - ((uint64_t)(int64_t)q << 40);
+    const float ang = (float)q * 3.7450703e-07f;               // * 2 pi 2^-24 (radians)
+    const float xr = (float)(int32_t)(r >> 9) * 1.7439342e-16f;
     float sn, cs;
     __sincosf(ang, &sn, &cs);
     const float re = fmaf(-xr, sn, cs);
