@@ -14,9 +14,12 @@
 //     buffers of H values;
 //  4. unpack X[k] = (Z[k] + conj Z[H-k])/2 - j/2 w^k (Z[k] - conj Z[H-k]),
 //     w = e^{-j 2 pi/N_FFT}, coalesced stores.
-// One CTA per trace; every twiddle (pre-twiddles, pass twiddles, the roots of
-// the odd radices, the unpack twiddle) comes from one float64-generated table
-// per plan.
+// F traces per CTA (a power-of-two number of threads per trace, about H/4,
+// each trace on its own named barrier); the pre-twiddles, pass twiddles and
+// unpack twiddles come from one float64-generated table per plan, the roots
+// of the odd radices are constants, and every index split (residue and
+// position, butterfly and twiddle index) is a float-reciprocal division with
+// one correction step instead of an integer division.
 #include "fft_block.cuh"
 #include "spec_internal.h"
 
@@ -24,7 +27,7 @@ namespace spec {
 
 namespace {
 
-constexpr int kMixedThreads = 512;
+constexpr int kMixedCta = 1024;       // threads per CTA at most (F traces of TT threads)
 
 // X[k] and X[H - k] from A = Z[k], B = Z[H - k] (the real-input unpack)
 __device__ __forceinline__ void unpack_pair_mixed(float2* Xr, int k, int H, float2 A, float2 B, float2 w) {
@@ -35,6 +38,18 @@ __device__ __forceinline__ void unpack_pair_mixed(float2* Xr, int k, int H, floa
     if (H - k != k) Xr[H - k] = make_float2(sp.x - wd.y, -sp.y - wd.x);
 }
 
+// q = x / d, x - q d for 0 <= x < 2^24 without an integer division: the
+// float quotient (reciprocal rounded, so off by at most one) and one
+// correction step
+__device__ __forceinline__ int fdivmod(int x, int d, float rcp, int* rem) {
+    int q = __float2int_rz((float)x * rcp);
+    int r = x - q * d;
+    if (r < 0) { --q; r += d; }
+    else if (r >= d) { ++q; r -= d; }
+    *rem = r;
+    return q;
+}
+
 struct MixedArgs {
     const float* x;
     int64_t batch;
@@ -42,101 +57,142 @@ struct MixedArgs {
     int64_t ld_x;
     float2* X;
     int64_t ld_X;
-    int H, LZ, R, npass;
-    int radix[kMixedMaxPasses];
-    const float2* tab;         // MixedPlan layout (offsets below)
-    int pre_off, pass_off, root_off, unpack_off;
+    int H, LZ, R, npass, TT, F;
+    float rLZ, rR;
+    int radix[kMixedMaxPasses], per[kMixedMaxPasses], ns[kMixedMaxPasses], twoff[kMixedMaxPasses];
+    float rper[kMixedMaxPasses], rns[kMixedMaxPasses];
+    const float2* tab;         // MixedPlan layout: pre-twiddles | pass twiddles | unpack
+    int pre_off, unpack_off;
 };
 
-// y = DFT_r(v) for an odd radix r (3, 5, 7) by its definition, with the
-// r roots e^{-j 2 pi i/r} from the table (root[i], i < r)
+// cos and sin of 2 pi m / r, m < r, for the odd radices
 template <int r>
-__device__ __forceinline__ void dft_odd(float2 (&v)[8], const float2* root) {
-    float2 w[r];
+__device__ __forceinline__ float root_c(int m) {
+    if constexpr (r == 3) return m == 0 ? 1.f : -0.5f;
+    else if constexpr (r == 5)
+        return m == 0 ? 1.f : (m == 1 || m == 4) ? 0.30901699437494745f : -0.8090169943749475f;
+    else
+        return m == 0 ? 1.f : (m == 1 || m == 6) ? 0.6234898018587336f
+                            : (m == 2 || m == 5) ? -0.22252093395631440f : -0.9009688679024191f;
+}
+template <int r>
+__device__ __forceinline__ float root_s(int m) {
+    if constexpr (r == 3) return m == 0 ? 0.f : m == 1 ? 0.8660254037844386f : -0.8660254037844386f;
+    else if constexpr (r == 5)
+        return m == 0 ? 0.f : m == 1 ? 0.9510565162951535f : m == 2 ? 0.5877852522924731f
+                            : m == 3 ? -0.5877852522924731f : -0.9510565162951535f;
+    else
+        return m == 0 ? 0.f : m == 1 ? 0.7818314824680298f : m == 2 ? 0.9749279121818236f
+                            : m == 3 ? 0.4338837391175581f : m == 4 ? -0.4338837391175581f
+                            : m == 5 ? -0.9749279121818236f : -0.7818314824680298f;
+}
+
+// y = DFT_r(v) (forward) for an odd radix, from the pair sums and
+// differences: X[k] = v0 + sum_i s_i cos(2 pi i k/r) - j sum_i d_i sin(2 pi i k/r),
+// s_i = v_i + v_{r-i}, d_i = v_i - v_{r-i}, and X[r-k] with the sine part negated
+template <int r>
+__device__ __forceinline__ void dft_odd(float2 (&v)[8]) {
+    constexpr int h = (r - 1) / 2;
+    float2 sm[h], df[h];
 #pragma unroll
-    for (int i = 0; i < r; ++i) w[i] = __ldg(root + i);
+    for (int i = 1; i <= h; ++i) {
+        sm[i - 1] = cadd(v[i], v[r - i]);
+        df[i - 1] = csub(v[i], v[r - i]);
+    }
     float2 y[r];
+    y[0] = v[0];
 #pragma unroll
-    for (int k = 0; k < r; ++k) {
-        float2 acc = v[0];
+    for (int i = 0; i < h; ++i) y[0] = cadd(y[0], sm[i]);
 #pragma unroll
-        for (int i = 1; i < r; ++i) acc = cadd(acc, cmul(v[i], w[(i * k) % r]));
-        y[k] = acc;
+    for (int k = 1; k <= h; ++k) {
+        float2 c = v[0], sj = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 1; i <= h; ++i) {
+            const float cc = root_c<r>((i * k) % r), ss = root_s<r>((i * k) % r);
+            c = make_float2(fmaf(cc, sm[i - 1].x, c.x), fmaf(cc, sm[i - 1].y, c.y));
+            sj = make_float2(fmaf(ss, df[i - 1].x, sj.x), fmaf(ss, df[i - 1].y, sj.y));
+        }
+        // -j sj = (sj.y, -sj.x)
+        y[k] = make_float2(c.x + sj.y, c.y - sj.x);
+        y[r - k] = make_float2(c.x - sj.y, c.y + sj.x);
     }
 #pragma unroll
     for (int k = 0; k < r; ++k) v[k] = y[k];
 }
 
-__device__ __forceinline__ void dft_any(int r, float2 (&v)[8], const float2* roots) {
+__device__ __forceinline__ void dft_any(int r, float2 (&v)[8]) {
     switch (r) {
         case 2: dft2<false>(v[0], v[1]); break;
         case 4: dft4<false>(v[0], v[1], v[2], v[3]); break;
         case 8: dft8<false>(v); break;
-        case 3: dft_odd<3>(v, roots); break;
-        case 5: dft_odd<5>(v, roots + 3); break;
-        default: dft_odd<7>(v, roots + 8); break;
+        case 3: dft_odd<3>(v); break;
+        case 5: dft_odd<5>(v); break;
+        default: dft_odd<7>(v); break;
     }
 }
 
-__global__ void __launch_bounds__(kMixedThreads) k_fft_mixed(MixedArgs a) {
+__global__ void __launch_bounds__(kMixedCta) k_fft_mixed(MixedArgs a) {
     extern __shared__ float2 smem[];
-    const int H = a.H, LZ = a.LZ, R = a.R;
-    float2* src = smem;
-    float2* dst = smem + H;
-    const int64_t b = blockIdx.x;
-    const float* xr = a.x + b * a.ld_x;
+    const int H = a.H, LZ = a.LZ, TT = a.TT;
+    const int f = threadIdx.x / TT;
+    const int tid = threadIdx.x - f * TT;
+    const int64_t b = (int64_t)blockIdx.x * a.F + f;
+    const bool live = b < a.batch;
+    // the F traces of a CTA synchronise on their own named barriers
+    const int bar = a.F > 1 ? 1 + f : 0;
+    float2* src = smem + (size_t)f * 2 * H;
+    float2* dst = src + H;
+    const float* xr = a.x + (live ? b : 0) * a.ld_x;
     const int n = a.n;
     // 1-2. packed, pre-twiddled input of every residue: src[r LZ + m]
-    for (int idx = threadIdx.x; idx < H; idx += kMixedThreads) {
-        const int r = idx / LZ;
-        const int m = idx - r * LZ;
-        const float re = 2 * m < n ? __ldg(xr + 2 * m) : 0.f;
-        const float im = 2 * m + 1 < n ? __ldg(xr + 2 * m + 1) : 0.f;
+    for (int idx = tid; idx < H; idx += TT) {
+        int m;
+        fdivmod(idx, LZ, a.rLZ, &m);
+        const float re = live && 2 * m < n ? __ldg(xr + 2 * m) : 0.f;
+        const float im = live && 2 * m + 1 < n ? __ldg(xr + 2 * m + 1) : 0.f;
         src[idx] = cmul(make_float2(re, im), __ldg(a.tab + a.pre_off + idx));
     }
-    __syncthreads();
+    group_sync(bar, TT);
     // 3. Stockham passes over all R residue DFTs at once
-    const float2* roots = a.tab + a.root_off;
-    int NS = 1, twoff = a.pass_off;
     for (int p = 0; p < a.npass; ++p) {
-        const int r = a.radix[p];
-        const int per = LZ / r;                 // butterflies per residue DFT
-        for (int bi = threadIdx.x; bi < H / r; bi += kMixedThreads) {
-            const int res = bi / per;
-            const int j = bi - res * per;
-            const int k = j % NS;
+        const int r = a.radix[p], per = a.per[p], NS = a.ns[p];
+        const float rper = a.rper[p], rns = a.rns[p];
+        const float2* tw = a.tab + a.twoff[p];
+        for (int bi = tid; bi < H / r; bi += TT) {
+            int j, k;
+            const int res = fdivmod(bi, per, rper, &j);
+            const int jk = fdivmod(j, NS, rns, &k);
             const float2* in = src + res * LZ + j;
             float2 v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i < r) v[i] = in[i * per];
             if (NS > 1) {
-                const float2* tw = a.tab + twoff + k;
 #pragma unroll
                 for (int i = 1; i < 8; ++i)
-                    if (i < r) v[i] = cmul(v[i], __ldg(tw + (i - 1) * NS));
+                    if (i < r) v[i] = cmul(v[i], __ldg(tw + (i - 1) * NS + k));
             }
-            dft_any(r, v, roots);
-            float2* out = dst + res * LZ + (j - k) * r + k;
+            dft_any(r, v);
+            float2* out = dst + res * LZ + jk * NS * r + k;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i < r) out[i * NS] = v[i];
         }
-        __syncthreads();
+        group_sync(bar, TT);
         float2* t = src;
         src = dst;
         dst = t;
-        if (NS > 1) twoff += (r - 1) * NS;
-        NS *= r;
     }
+    if (!live) return;
     // 4. unpack the pairs (k, H - k); Z[k] = src[(k mod R) LZ + k / R]
     float2* Xr = a.X + b * a.ld_X;
     const float2* wk = a.tab + a.unpack_off;
-    for (int k = threadIdx.x; k <= H / 2; k += kMixedThreads) {
+    for (int k = tid; k <= H / 2; k += TT) {
         const int km = k == 0 ? 0 : H - k;
-        const float2 A = src[(k % R) * LZ + k / R];
-        const float2 B = src[(km % R) * LZ + km / R];
-        unpack_pair_mixed(Xr, k, H, A, B, __ldg(wk + k));
+        int ra, rb;
+        const int qa = fdivmod(k, a.R, a.rR, &ra);
+        const int qb = fdivmod(km, a.R, a.rR, &rb);
+        unpack_pair_mixed(Xr, k, H, src[ra * LZ + qa], src[rb * LZ + qb], __ldg(wk + k));
     }
 }
 
@@ -178,7 +234,7 @@ bool mixed_plan(int64_t n, int64_t n_fft, MixedPlan* p, std::string* why) {
         p->LZ = (int)LZ;
         p->R = (int)(H / LZ);
         p->radix = rad;
-        // table: pre-twiddles [R][LZ] | pass twiddles | roots of 3, 5, 7 | unpack
+        // table: pre-twiddles [R][LZ] | pass twiddles | unpack
         int pass = 0, ns = 1;
         for (int r : rad) {
             if (ns > 1) pass += (r - 1) * ns;
@@ -187,7 +243,7 @@ bool mixed_plan(int64_t n, int64_t n_fft, MixedPlan* p, std::string* why) {
         p->pre_off = 0;
         p->pass_off = (int)H;
         p->root_off = p->pass_off + pass;
-        p->unpack_off = p->root_off + 15;
+        p->unpack_off = p->root_off;
         p->entries = p->unpack_off + (int)(H / 2) + 1;
         p->smem = (size_t)2 * H * sizeof(float2);
         return true;
@@ -213,9 +269,6 @@ void mixed_fill_table(const MixedPlan& p, float2* host) {
         if (ns > 1) off += (r - 1) * ns;
         ns *= r;
     }
-    int q = p.root_off;
-    for (int r : {3, 5, 7})
-        for (int i = 0; i < r; ++i) host[q++] = w(i, r);
     for (int64_t k = 0; k <= H / 2; ++k) host[p.unpack_off + k] = w(k, 2 * H);
 }
 
@@ -225,12 +278,33 @@ cudaError_t mixed_launch(const MixedPlan& p, const float* x, int64_t batch, int 
     MixedArgs a = {};
     a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x; a.X = X; a.ld_X = ld_X;
     a.H = p.H; a.LZ = p.LZ; a.R = p.R; a.npass = (int)p.radix.size();
-    for (size_t i = 0; i < p.radix.size(); ++i) a.radix[i] = p.radix[i];
+    a.rLZ = 1.0f / (float)p.LZ;
+    a.rR = 1.0f / (float)p.R;
+    // threads per trace: about a quarter of H (a radix-4 pass in one sweep), a
+    // power of two in [32, 1024]; short traces share a CTA of 256 threads (at
+    // most 4 traces, one named barrier each)
+    int TT = 32;
+    while (TT < kMixedCta && TT < (p.H + 3) / 4) TT *= 2;
+    a.TT = TT;
+    a.F = std::max(1, std::min(4, 256 / TT));
+    int ns = 1, off = p.pass_off;
+    for (size_t i = 0; i < p.radix.size(); ++i) {
+        const int r = p.radix[i];
+        a.radix[i] = r;
+        a.per[i] = p.LZ / r;
+        a.ns[i] = ns;
+        a.rper[i] = 1.0f / (float)a.per[i];
+        a.rns[i] = 1.0f / (float)ns;
+        a.twoff[i] = off;
+        if (ns > 1) off += (r - 1) * ns;
+        ns *= r;
+    }
     a.tab = tab;
-    a.pre_off = p.pre_off; a.pass_off = p.pass_off; a.root_off = p.root_off; a.unpack_off = p.unpack_off;
-    cudaError_t e = cudaFuncSetAttribute(k_fft_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    a.pre_off = p.pre_off; a.unpack_off = p.unpack_off;
+    const size_t smem = (size_t)a.F * 2 * p.H * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_mixed<<<(unsigned)batch, kMixedThreads, p.smem, st>>>(a);
+    k_fft_mixed<<<(unsigned)((batch + a.F - 1) / a.F), a.F * TT, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -589,7 +589,25 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
             c->fft.push_back(ne);
             tab = ne.tab;
         }
-        cudaError_t e = mixed_launch(mp, x, batch, (int)n, ld_x, tab, reinterpret_cast<float2*>(X), ld_X, st);
+        // the mixed-radix kernel or the chirp-z on the DFT grid, whichever
+        // measures faster for this shape (SPEC_FFT_VARIANT pins one)
+        spec_status sc = SPEC_OK;
+        auto run = [&](int i) {
+            if (i == 0) return mixed_launch(mp, x, batch, (int)n, ld_x, tab, reinterpret_cast<float2*>(X), ld_X, st);
+            sc = spec_czt(c, x, batch, n, ld_x, fs, 0.0, fs * (double)(bins - 1) / (double)n_fft, bins,
+                          SPEC_CZT_AUTO, X, ld_X, stream);
+            return sc == SPEC_OK ? cudaSuccess : cudaErrorUnknown;
+        };
+        const std::vector<std::string> names{"mixed", "dftczt"};
+        int pick = -1;
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == c->fft_variant) pick = (int)i;
+        if (pick < 0) {
+            pick = tune_pick(c, tune_key("fftmixed", {n_fft, mp.LZ}), names, run, st, &s);
+            if (pick < 0) return s == SPEC_OK ? fail(c, SPEC_ECUDA, "spec_fft variant timing") : s;
+        }
+        cudaError_t e = run(pick);
+        if (pick == 1 && sc != SPEC_OK) return sc;
         if (e != cudaSuccess) return cuda_fail(c, e, "spec_fft mixed-radix launch");
         return SPEC_OK;
     }

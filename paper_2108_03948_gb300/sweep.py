@@ -8,8 +8,9 @@ that shape (one launch sequence per method), timed with CUDA events.
 
 Per resolution Delta f:
   FFT   N_FFT = ceil(fs / Delta f) (Eq. 3; the zeros of Eq. 5 are N_FFT - N),
-        any length (powers of two run the padded FFT, others the chirp-z on
-        the DFT grid);
+        any length (powers of two run the padded FFT, even lengths whose half
+        has only the factors 2, 3, 5, 7 the mixed-radix padded FFT, others the
+        chirp-z on the DFT grid);
   CZT   the band f1 .. f2 at M = ceil((f2 - f1) N_FFT / fs) points (Eq. 25);
   Zoom  the same band, decimation D the largest power of two with
         fs / D >= 1.25 (f2 - f1), K = N_FFT / D rounded up to a power of two

@@ -374,3 +374,20 @@ def test_zoom_and_bluestein_lane_forms_parity(S, monkeypatch, lanes):
             got = S.spec_czt(c, dev(x), fs, f1, f2, m, mode=S.SPEC_CZT_BLUESTEIN).cpu().numpy()
             err = rel_rows(got, O.czt(x, fs, f1, f2, m))
             assert err.max() <= TOL, (lanes, batch, n, m, err.max())
+
+
+MIXED_CASES = [(4, 500, 2000), (3, 500, 10000), (2, 500, 20000), (3, 1000, 2000), (5, 333, 1050), (3, 12, 42),
+               (2, 1, 6), (3, 4000, 26460), (9, 500, 500), (6, 700, 1250)]
+
+
+@pytest.mark.parametrize("variant", ["mixed", "dftczt"])
+def test_fft_non_power_of_two_forms_parity(S, monkeypatch, variant):
+    # lengths whose half has only the factors 2, 3, 5, 7: the mixed-radix
+    # kernel or the chirp-z on the DFT grid, pinned (the autotuner times both)
+    monkeypatch.setenv("SPEC_FFT_VARIANT", variant)
+    with S.Context(0) as c:
+        for batch, n, n_fft in MIXED_CASES:
+            x = traces(batch, n, 5 * n + n_fft)
+            got = S.spec_fft(c, dev(x), 20e12, n_fft).cpu().numpy()
+            err = rel_rows(got, O.fft_padded(x, n_fft))
+            assert err.max() <= TOL, (variant, batch, n, n_fft, err.max())
