@@ -248,6 +248,33 @@ class NvmlClocks:
         return float(mhz.value), mw.value / 1e3, int(rs.value)
 
 
+def bind_near_gpu(cuda_index):
+    """Restrict this process to the host cores NVML reports as local to the
+    GPU (nvmlDeviceGetCpuAffinity) while the end-to-end leg allocates its
+    pinned host buffers, so that they land on the memory node attached to the
+    GPU rather than across the CPU-to-CPU link (pages stay where they were
+    first placed; the caller restores the affinity afterwards).  Only this
+    process's own affinity changes.  Returns ({"cpus": n, "of": total}, the
+    previous affinity) or (None, None) when NVML does not say."""
+    prev = os.sched_getaffinity(0)
+    try:
+        import ctypes
+        nv = NvmlClocks(cuda_index)
+        words = 16
+        arr = (ctypes.c_ulong * words)()
+        if nv.lib.nvmlDeviceGetCpuAffinity(nv.h, words, arr) != 0:
+            return None, None
+        bits = 8 * ctypes.sizeof(ctypes.c_ulong)
+        cpus = {w * bits + b for w in range(words) for b in range(bits) if (arr[w] >> b) & 1}
+        mine = cpus & prev
+        if not mine or mine == prev:
+            return {"cpus": len(prev), "of": len(prev)}, prev
+        os.sched_setaffinity(0, mine)
+        return {"cpus": len(mine), "of": len(prev)}, prev
+    except (OSError, AttributeError):
+        return None, None
+
+
 class ClockSampler:
     """Clocks and throttle reasons during the timed region: NVML every 1 ms
     when the library loads, else nvidia-smi every 100 ms.  Samples go to a CSV
@@ -817,17 +844,26 @@ def measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, scaling):
     value = job_throughput(bins_all, steps, total_ms / 1e3)
     launches = W.launches()
 
+    affinity, prev_affinity = bind_near_gpu(dev.index)
     e2e_step, e2e_check, h2d, d2h = W.e2e()
     e2e_step()
     torch.cuda.synchronize()
     e2e_steps = max(1, min(steps, 10))
     if world > 1:
         torch.distributed.barrier()
-    t0 = time.perf_counter()
+    # each step returns only when its spectra are in host memory; the host
+    # link is shared with the machine's other tenants, so the per-step median
+    # is the figure (the mean is reported beside it)
+    e2e_ts = []
     for _ in range(e2e_steps):
+        t0 = time.perf_counter()
         e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        torch.cuda.synchronize()
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_mean = max_over_ranks(sum(e2e_ts) / len(e2e_ts), world, dev)
+    e2e_s = max_over_ranks(statistics.median(e2e_ts), world, dev) * e2e_steps
+    if prev_affinity is not None:
+        os.sched_setaffinity(0, prev_affinity)
     e2e_val = job_throughput(bins_all, e2e_steps, e2e_s)
     e2e_diff = e2e_check()
     e2e_ms = 1e3 * e2e_s / e2e_steps
@@ -838,7 +874,9 @@ def measure_workload(wl, args, steps, ctx_tuple, peaks, want_cpu, scaling):
            "ms_per_step": statistics.mean(step_ms), "bins_per_step_per_gpu": bins_step, "share": share,
            "kernels": kern, "roofline": roofline_of(kern, wl, peaks), "gpu_launches_per_step": launches,
            "e2e": {"value": e2e_val, "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "steps": e2e_steps, "ms_per_step": e2e_ms, "max_abs_diff_vs_device_path": e2e_diff}}
+                   "steps": e2e_steps, "ms_per_step": e2e_ms, "ms_per_step_mean": 1e3 * e2e_mean,
+                   "statistic": "median of the steps", "max_abs_diff_vs_device_path": e2e_diff},
+           "host_affinity": affinity}
     if wl == 2:
         # which form each transform's plan runs (the persistent work queue or
         # the per-shape launches), as timed when the plan was built
@@ -1004,6 +1042,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": h["gpu_launches_per_step"] * h["steps"],
         "clocks": clocks.summary(),
+        "host_affinity": h.get("host_affinity"),
         "library_comparison": lib_cmp,
         "workloads": others,
         "wall_s": wall,
