@@ -30,6 +30,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "mbarrier.cuh"
@@ -44,7 +46,11 @@ constexpr int TILE_B = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;               // 2 buffers x (D1, D2) x 128 columns
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+// epilogue staging for bulk tensor stores: per epilogue warp two 32 x 32
+// float boxes (4 KB each, rows of 128 bytes in the 128-byte swizzle)
+constexpr int OUT_BOX = 32 * 32 * 4;
+constexpr int OUT_BYTES = 4 * 2 * OUT_BOX;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + OUT_BYTES + 1024 + 256;
 
 // Instruction descriptor, kind::f16: FP32 accumulate (bits 4-5 = 1), A and B
 // FP16 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at
@@ -61,6 +67,21 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
 }
+
+// Bulk tensor store of a shared-memory box to global memory (bulk group).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most N bulk groups still reading their shared-memory source
+template <int N> __device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes visible to the asynchronous proxy
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
 // rows of 64 FP16 (128 B), 8-row groups 1024 B apart (stride byte offset),
@@ -110,16 +131,20 @@ struct GemmArgs {
     const int* col_pow;        // per output bin k: log2 of Z's column scale (spiral contours), or null
     float* out;
     int64_t ld_out;            // floats
+    int vec4;                  // rows and base 16-byte aligned: 16-byte stores
+    int tma_out;               // mOut describes out: bulk tensor stores from shared memory
     unsigned* status;
     uint64_t timeout_ns;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_czt_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, GemmArgs a) {
+               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+               const __grid_constant__ CUtensorMap mOut, GemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(base + STAGES * STAGE_BYTES);
+    uint8_t* obuf = base + STAGES * STAGE_BYTES;               // 1024-byte aligned
+    uint64_t* full = (uint64_t*)(obuf + OUT_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + 2;
@@ -241,6 +266,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int q = warp & 3;
         int acc = 0;
         uint32_t aph = 0;
+        int nbox = 0;                                    // boxes this warp has stored
         for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
             if (!wait_bounded(tfull + acc, aph, g)) break;
             tc_fence_after();
@@ -257,7 +283,57 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tmem_ld32(tbase + c * 32, r1);
                 if (a.terms == 3) tmem_ld32(tbase + 128 + c * 32, r2);
                 tmem_ld_wait();
-                if (live) {
+                if (a.tma_out) {
+                    // stage the warp's 32 x 32 box (row = lane, 128-byte
+                    // swizzle: 16-byte chunk u of row r at u ^ (r mod 8)) and
+                    // store it with one bulk tensor copy; rows beyond the
+                    // batch and columns beyond 2M are clipped by the copy
+                    uint8_t* box = obuf + (size_t)(q * 2 + (nbox & 1)) * OUT_BOX;
+                    if (nbox >= 2) {
+                        if (lane == 0) bulk_wait_read<1>();         // this buffer's last store has read it
+                        __syncwarp();
+                    }
+                    const int colb = n0 + c * 32;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        float v[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            v[e] = __uint_as_float(r1[4 * u + e]);
+                            if (a.terms == 3) v[e] = fmaf(__uint_as_float(r2[4 * u + e]), 4.8828125e-4f, v[e]);
+                        }
+                        const int k0 = (colb + 4 * u) >> 1;        // output bins of the chunk's columns
+                        const float s0 = a.col_pow && live ? ldexpf(1.0f, -14 - rp + a.col_pow[min(k0, a.cols / 2 - 1)]) : scale;
+                        const float s1 = a.col_pow && live ? ldexpf(1.0f, -14 - rp + a.col_pow[min(k0 + 1, a.cols / 2 - 1)]) : scale;
+                        *(float4*)(box + lane * 128 + ((u ^ (lane & 7)) << 4)) =
+                            make_float4(v[0] * s0, v[1] * s0, v[2] * s1, v[3] * s1);
+                    }
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane == 0) {
+                        // a box wholly past the batch is not stored (only
+                        // boxes that start inside the tensor are issued)
+                        const int64_t row0 = (tile / a.ntn) * BM + q * 32;
+                        if (row0 < a.rows && colb < a.cols) tma_store_2d(&mOut, box, colb, (int)row0);
+                        bulk_commit();
+                    }
+                    ++nbox;
+                } else if (live && a.vec4 && n0 + c * 32 + 32 <= a.cols) {
+                    // whole 32-column chunk inside the output: 16-byte stores
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const int col = n0 + c * 32 + j;
+                        float v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            v[u] = __uint_as_float(r1[j + u]);
+                            if (a.terms == 3) v[u] = fmaf(__uint_as_float(r2[j + u]), 4.8828125e-4f, v[u]);   // 2^-11
+                        }
+                        const float s0 = a.col_pow ? ldexpf(1.0f, -14 - rp + a.col_pow[col >> 1]) : scale;
+                        const float s1 = a.col_pow ? ldexpf(1.0f, -14 - rp + a.col_pow[(col >> 1) + 1]) : scale;
+                        *(float4*)(orow + col) = make_float4(v[0] * s0, v[1] * s0, v[2] * s1, v[3] * s1);
+                    }
+                } else if (live) {
 #pragma unroll
                     for (int j = 0; j < 32; j += 2) {
                         const int col = n0 + c * 32 + j;
@@ -278,6 +354,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_arrive(tempty + acc);
             if (++acc == 2) { acc = 0; aph ^= 1u; }
         }
+        // every bulk store of this warp complete before the CTA (and its
+        // shared memory) goes away
+        if (a.tma_out && lane == 0) bulk_wait_all();
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -393,6 +473,20 @@ EncodeFn encode_fn() {
 }
 
 // 2-D FP16 tensor [rows][np], boxes of 128 rows x 64 columns, 128-byte swizzle
+// Output [rows][cols] float32 at a row pitch of ld floats, stored in 32 x 32
+// boxes with the 128-byte swizzle (the epilogue's staging layout).
+bool make_out_map(CUtensorMap* map, float* ptr, int64_t rows, int cols, int64_t ld) {
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_map(CUtensorMap* map, const __half* ptr, int64_t rows, int np) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
@@ -403,6 +497,15 @@ bool make_map(CUtensorMap* map, const __half* ptr, int64_t rows, int np) {
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)ptr, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// SPEC_GEMM_TMA_OUT=0 keeps the per-thread 16-byte stores (for comparison)
+bool tma_out_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("SPEC_GEMM_TMA_OUT");
+        return !(e && std::atoi(e) == 0);
+    }();
+    return on;
 }
 
 }  // namespace
@@ -473,12 +576,16 @@ cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, cons
     a.col_pow = col_pow;
     a.out = (float*)X;
     a.ld_out = 2 * ld_X;
+    a.vec4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && (a.ld_out & 3) == 0) ? 1 : 0;
+    CUtensorMap mOut;
+    std::memset(&mOut, 0, sizeof(mOut));
+    a.tma_out = (a.vec4 && tma_out_enabled() && make_out_map(&mOut, a.out, batch, a.cols, a.ld_out)) ? 1 : 0;
     a.status = status;
     a.timeout_ns = timeout_ns;
     cudaError_t e = cudaFuncSetAttribute(k_czt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.tiles, (int64_t)std::max(1, sms));
-    k_czt_gemm<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a);
+    k_czt_gemm<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, mOut, a);
     return cudaGetLastError();
 }
 

@@ -252,3 +252,18 @@ def test_spiral_czt_rejections(ctx, S):
     assert lib.spec_czt_spiral(*args, 1.0, -1.0, X.data_ptr(), 64, None) == S.SPEC_EINVAL
     assert lib.spec_czt_spiral(*args, 0.5, 1.0, X.data_ptr(), 64, None) == S.SPEC_EUNSUPPORTED   # 2^999
     assert np.all(X.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("batch,m,ld", [(300, 512, 600), (129, 100, 104), (131, 48, 48)])
+def test_gemm_output_pitch_and_edges(ctx, S, batch, m, ld):
+    # the product's epilogue stores 32 x 32 boxes with bulk tensor copies when
+    # the output rows are 16-byte aligned: a row pitch wider than M, a batch
+    # that ends inside a 128-row tile and 2M not a multiple of 32 must all
+    # leave every byte outside the spectra untouched
+    x = noise(batch, 1000, batch + m)
+    out = torch.full((batch, ld), complex(float("nan"), float("nan")), dtype=torch.complex64, device="cuda")
+    S.spec_czt(ctx, dev(x), FS, 0.3e12, 2.2e12, m, mode=S.SPEC_CZT_GEMM_F16X3, out=out)
+    got = out.cpu().numpy()
+    assert rel(got[:, :m], O.czt(x, FS, 0.3e12, 2.2e12, m)).max() <= TOL
+    if ld > m:
+        assert np.isnan(got[:, m:].real).all() and np.isnan(got[:, m:].imag).all()
