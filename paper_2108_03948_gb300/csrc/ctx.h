@@ -54,6 +54,7 @@ struct spec_ctx {
                                          // chirp-z and Zoom: measured fastest); 1 or 2: forced everywhere
     bool fft_cluster = false;            // SPEC_FFT_CLUSTER=1: long traces on k_fft_real_cluster
     std::string fft_variant;             // SPEC_FFT_VARIANT: pin a padded-FFT kernel variant by name
+    bool gemm_fused = false;             // SPEC_GEMM_FUSED=1: FP16 split inside the tensor-core product
     int ragged_queue = -1;               // SPEC_RAGGED_QUEUE: 1 always / 0 never the work queue, -1 timed
     std::map<std::string, std::string> tune;   // SPEC_CZT_AUTO decisions ("czt n=.. m=.. b=.." -> mode)
     std::string tune_path, tune_device;        // SPEC_AUTOTUNE_CACHE file and this device's tag

@@ -45,6 +45,11 @@ constexpr int TILE_A = BM * BK * 2;               // bytes of one FP16 part of a
 constexpr int TILE_B = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int THREADS = 192;
+// with the FP16 split fused into the product: four more warps convert each
+// staged FP32 x tile in place into the parts the tensor cores read
+constexpr int THREADS_FUSED = 448;
+constexpr int NCONV = THREADS_FUSED - 192;       // converter threads (8 warps)
+constexpr int CONV0 = 192;                        // first converter thread
 constexpr uint32_t TMEM_COLS = 512;               // 2 buffers x (D1, D2) x 128 columns
 // epilogue staging for bulk tensor stores: per epilogue warp two 32 x 32
 // float boxes (4 KB each, rows of 128 bytes in the 128-byte swizzle)
@@ -137,7 +142,94 @@ struct GemmArgs {
     uint64_t timeout_ns;
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+// Barrier 1 of the NCONV converter threads, returning the OR of `pred` over them.
+__device__ __forceinline__ bool bar_or_conv(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(NCONV)
+        : "memory");
+    return r != 0;
+}
+
+// FUSED converter (NCONV = 256 threads, ct < 256): for every stage in the
+// order the producer fills them, wait for the FP32 x box (128 rows x 64
+// samples, rows of 256 bytes), scale row r by 2^row_pow[r] and split it into
+// the FP16 parts (the arithmetic of k_gemm_split_x, so the parts are the same
+// bits), then, once all converter threads have read the box, write the parts
+// over it in the K-major 128-byte-swizzled layout the product reads (part h
+// at the stage's A area, part l at A + TILE_A), make the writes visible to the
+// tensor cores and arrive on conv.  Thread ct owns 16-byte chunk ct mod 8 of
+// rows ct/8 + 32 i (i < 4): a quarter-warp reads 128 contiguous bytes and
+// writes one swizzled 128-byte row, both without bank conflicts.
+__device__ __forceinline__ void convert_stages(const GemmArgs& a, uint8_t* base, uint64_t* full, uint64_t* conv,
+                                               const Guard& g, int ct) {
+    constexpr int ROWS = NCONV / 8, PER = BM / ROWS;        // 32 rows a sweep, 4 sweeps
+    const int ch = ct & 7;
+    const int hsel = (ch >> 2) & 1;              // which 16-byte half is read first (spreads the banks)
+    int stage = 0;
+    uint32_t ph = 0;
+    for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+        const int64_t m0 = (tile / a.ntn) * BM;
+        float sc[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int64_t row = m0 + (ct >> 3) + ROWS * i;
+            sc[i] = row < a.rows ? ldexpf(1.0f, a.row_pow[row]) : 0.f;
+        }
+        for (int kb = 0; kb < a.kblocks; ++kb) {
+            // a wait that gives up is acted on by all converter threads
+            // together (at the barrier below), so that none is left waiting
+            const bool okw = wait_bounded(full + stage, ph, g);
+            uint8_t* sa = base + stage * STAGE_BYTES;
+            uint4 hi[PER], lo[PER];
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int r = (ct >> 3) + ROWS * i;
+                const float4* src = reinterpret_cast<const float4*>(sa + r * 256 + ch * 32);
+                const float4 f0 = src[hsel], f1 = src[hsel ^ 1];
+                const float4 q0 = hsel ? f1 : f0, q1 = hsel ? f0 : f1;
+                const float2 xv[4] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                      make_float2(q1.z, q1.w)};
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 v = make_float2(xv[e].x * sc[i], xv[e].y * sc[i]);
+                    if (a.terms < 0) {
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v.x, v.y);
+                        hw[e] = *reinterpret_cast<const uint32_t*>(&b2);
+                        lw[e] = 0;
+                    } else {
+                        const __half2 h2 = __floats2half2_rn(v.x, v.y);
+                        const float2 hb = __half22float2(h2);
+                        const __half2 l2 = __floats2half2_rn((v.x - hb.x) * 2048.f, (v.y - hb.y) * 2048.f);
+                        hw[e] = *reinterpret_cast<const uint32_t*>(&h2);
+                        lw[e] = *reinterpret_cast<const uint32_t*>(&l2);
+                    }
+                }
+                hi[i] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                lo[i] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            // every converter thread has read the box before any part
+            // overwrites it; the same barrier ORs the threads' wait failures
+            if (bar_or_conv(!okw)) return;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int r = (ct >> 3) + ROWS * i;
+                const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+                *reinterpret_cast<uint4*>(sa + off) = hi[i];
+                if (a.terms == 3) *reinterpret_cast<uint4*>(sa + TILE_A + off) = lo[i];
+            }
+            fence_async_shared();
+            mbar_arrive(conv + stage);
+            if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+        }
+    }
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(FUSED ? THREADS_FUSED : THREADS, 1)
     k_czt_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                const __grid_constant__ CUtensorMap mOut, GemmArgs a) {
@@ -149,7 +241,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + 2;
     uint64_t* done = tempty + 2;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    uint64_t* conv = done + 1;                   // FUSED: stage converted (NCONV arrivals)
+    uint32_t* tmem_slot = (uint32_t*)(conv + STAGES);
     int* abort_flag = (int*)(tmem_slot + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -157,6 +250,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
+            mbar_init(conv + s, NCONV);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(tfull + i, 1);
@@ -177,7 +271,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const Guard g{abort_flag, a.status, a.timeout_ns};
-    const uint32_t stage_tx = a.terms == 3 ? (uint32_t)STAGE_BYTES : (uint32_t)(TILE_A + TILE_B);
+    // FUSED: the A part of a stage is one 128 x 64 FP32 box of x (both FP16
+    // parts' space); otherwise the FP16 parts made by k_gemm_split_x
+    const uint32_t stage_tx = FUSED ? (uint32_t)(2 * TILE_A + (a.terms == 3 ? 2 : 1) * TILE_B)
+                                    : a.terms == 3 ? (uint32_t)STAGE_BYTES : (uint32_t)(TILE_A + TILE_B);
     const uint32_t idesc = a.terms < 0 ? kIdescBf16 : kIdesc;
 
     if (warp == 0) {
@@ -198,7 +295,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tma_load_2d(sa, &mAh, full + stage, kb * BK, m0);
                     tma_load_2d(sa + 2 * TILE_A, &mBh, full + stage, kb * BK, n0);
                     if (a.terms == 3) {
-                        tma_load_2d(sa + TILE_A, &mAl, full + stage, kb * BK, m0);
+                        if (!FUSED) tma_load_2d(sa + TILE_A, &mAl, full + stage, kb * BK, m0);
                         tma_load_2d(sa + 2 * TILE_A + TILE_B, &mBl, full + stage, kb * BK, n0);
                     }
                     issued_ph[stage] = (int)ph;
@@ -229,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t d1 = tmem + (uint32_t)(acc * 256);
                 const uint32_t d2 = d1 + 128;
                 for (int kb = 0; kb < a.kblocks; ++kb) {
-                    if (!wait_bounded(full + stage, ph, g)) { ok = false; break; }
+                    if (!wait_bounded((FUSED ? conv : full) + stage, ph, g)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(base + stage * STAGE_BYTES);
 #pragma unroll
@@ -261,6 +358,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
         }
+    } else if (FUSED && warp >= CONV0 / 32) {
+        convert_stages(a, base, full, conv, g, threadIdx.x - CONV0);
     } else {
         // epilogue, warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31
         const int q = warp & 3;
@@ -399,6 +498,30 @@ __global__ void k_gemm_split_x(const float* x, int64_t batch, int n, int64_t ld_
     if (lane == 0) row_pow[row] = p;
 }
 
+// The row exponents alone (for the product with the split fused in): one
+// warp per row, p = min(127, 15 - e) with max |x| < 2^e, as k_gemm_split_x.
+__global__ void k_gemm_row_pow(const float* x, int64_t batch, int n, int64_t ld_x, int* row_pow, int v4) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (row >= batch) return;
+    const float* xr = x + row * ld_x;
+    float mx = 0.f;
+    if (v4) {                                    // n, the rows and x all 16-byte multiples
+        const float4* x4 = reinterpret_cast<const float4*>(xr);
+        for (int i = lane; i < n / 4; i += 32) {
+            const float4 v = __ldg(x4 + i);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+    } else {
+        for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(__ldg(xr + i)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.f && mx <= 3.4e38f) frexpf(mx, &e);
+    if (lane == 0) row_pow[row] = min(127, 15 - e);
+}
+
 // Z rows c < 2M (cos for c = 2k, -sin for c = 2k+1) at the exact phase
 // A n + B k n (64-bit fixed point, cycles), scaled by 2^14 and split (or, for
 // the BF16 form, rounded once to BF16 into zh; zl then holds zeros).
@@ -487,6 +610,21 @@ bool make_out_map(CUtensorMap* map, float* ptr, int64_t rows, int cols, int64_t 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// x itself, [rows][n] float32 at a row pitch of ld floats, in 128 x 64
+// boxes without swizzle (the converter reads 256-byte rows); samples past n
+// read as zeros.
+bool make_x_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t n, int64_t ld) {
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t box[2] = {BK, BM};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_map(CUtensorMap* map, const __half* ptr, int64_t rows, int np) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
@@ -550,9 +688,22 @@ cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t 
     return cudaGetLastError();
 }
 
+bool gemm_fused_ok(const float* x, int64_t ld_x) {
+    return (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ld_x & 3) == 0;
+}
+
+cudaError_t gemm_rowpow_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, void* work, cudaStream_t st) {
+    if (batch == 0) return cudaSuccess;
+    const int np = gemm_padded_n(n);
+    int* row_pow = (int*)((uint8_t*)work + ((size_t)2 * batch * np * sizeof(__half) + 255) / 256 * 256);
+    const bool v4 = (n & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ld_x & 3) == 0;
+    k_gemm_row_pow<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>(x, batch, (int)n, ld_x, row_pow, v4 ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, const void* z, const void* work,
                             float2* X, int64_t ld_X, unsigned* status, int sms, uint64_t timeout_ns,
-                            cudaStream_t st, const int* col_pow) {
+                            cudaStream_t st, const int* col_pow, const float* x, int64_t ld_x) {
     if (batch == 0) return cudaSuccess;
     const int np = gemm_padded_n(n);
     const __half* xh = (const __half*)work;
@@ -561,10 +712,15 @@ cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, cons
         (const int*)((const uint8_t*)work + ((size_t)2 * batch * np * sizeof(__half) + 255) / 256 * 256);
     const __half* zh = (const __half*)z;
     const __half* zl = zh + (size_t)2 * m * np;
+    const bool fused = x != nullptr;
     CUtensorMap mAh, mAl, mBh, mBl;
-    if (!make_map(&mAh, xh, batch, np) || !make_map(&mAl, xl, batch, np) || !make_map(&mBh, zh, 2 * m, np) ||
-        !make_map(&mBl, zl, 2 * m, np))
+    if (fused) {
+        if (!make_x_map(&mAh, x, batch, n, ld_x)) return cudaErrorInvalidValue;
+        mAl = mAh;
+    } else if (!make_map(&mAh, xh, batch, np) || !make_map(&mAl, xl, batch, np)) {
         return cudaErrorInvalidValue;
+    }
+    if (!make_map(&mBh, zh, 2 * m, np) || !make_map(&mBl, zl, 2 * m, np)) return cudaErrorInvalidValue;
     GemmArgs a = {};
     a.rows = batch;
     a.cols = (int)(2 * m);
@@ -582,10 +738,12 @@ cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, cons
     a.tma_out = (a.vec4 && tma_out_enabled() && make_out_map(&mOut, a.out, batch, a.cols, a.ld_out)) ? 1 : 0;
     a.status = status;
     a.timeout_ns = timeout_ns;
-    cudaError_t e = cudaFuncSetAttribute(k_czt_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    const void* kf = fused ? (const void*)k_czt_gemm<true> : (const void*)k_czt_gemm<false>;
+    cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(a.tiles, (int64_t)std::max(1, sms));
-    k_czt_gemm<<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, mOut, a);
+    if (fused) k_czt_gemm<true><<<(unsigned)grid, THREADS_FUSED, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, mOut, a);
+    else k_czt_gemm<false><<<(unsigned)grid, THREADS, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, mOut, a);
     return cudaGetLastError();
 }
 

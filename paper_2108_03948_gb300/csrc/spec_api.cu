@@ -359,10 +359,17 @@ spec_status czt_gemm(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
     if ((s = ensure_stage(c, 3, gemm_work_bytes(chunk, n))) != SPEC_OK) return s;
     for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
         const int64_t nb = std::min(chunk, batch - b0);
-        cudaError_t e = gemm_split_launch(x + b0 * ld_x, nb, n, ld_x, terms, c->stage[3], st);
+        // the FP16 split as a pass of its own, then the product; with
+        // SPEC_GEMM_FUSED=1 the split runs inside the product instead (FP32
+        // boxes of x by TMA, converter warps; only the row exponents are a
+        // pass), measured slower on GB300 and therefore not the default
+        const float* xb = x + b0 * ld_x;
+        const bool fused = c->gemm_fused && gemm_fused_ok(xb, ld_x);
+        cudaError_t e = fused ? gemm_rowpow_launch(xb, nb, n, ld_x, c->stage[3], st)
+                              : gemm_split_launch(xb, nb, n, ld_x, terms, c->stage[3], st);
         if (e == cudaSuccess)
             e = gemm_mul_launch(nb, n, m, terms, en->z, c->stage[3], X2 + b0 * ld_X, ld_X, c->status, c->sms,
-                                c->wait_timeout_ns, st, en->col_pow);
+                                c->wait_timeout_ns, st, en->col_pow, fused ? xb : nullptr, ld_x);
         if (e != cudaSuccess) return cuda_fail(c, e, "GEMM chirp-z launch");
     }
     return SPEC_OK;
@@ -450,6 +457,7 @@ spec_status spec_ctx_create(spec_ctx** ctx, int device) {
     if (const char* ev = std::getenv("SPEC_LANES")) c->lanes = std::atoi(ev);
     if (const char* ev = std::getenv("SPEC_FFT_CLUSTER")) c->fft_cluster = std::atoi(ev) == 1;
     if (const char* ev = std::getenv("SPEC_FFT_VARIANT")) c->fft_variant = ev;
+    if (const char* ev = std::getenv("SPEC_GEMM_FUSED")) c->gemm_fused = std::atoi(ev) == 1;
     if (const char* ev = std::getenv("SPEC_RAGGED_QUEUE")) c->ragged_queue = std::atoi(ev) == 1 ? 1 : 0;
     c->tune_device = device_tag(device);
     if (const char* ev = std::getenv("SPEC_AUTOTUNE_CACHE")) {

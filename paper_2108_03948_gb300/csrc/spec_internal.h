@@ -186,9 +186,15 @@ cudaError_t gemm_build_z(int64_t n, int64_t m, uint64_t A, uint64_t B, void* z, 
 // (gemm_work_bytes(batch, n)); the product reads them.
 cudaError_t gemm_split_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, int terms, void* work,
                               cudaStream_t st);
+// x != null: the split runs inside the product (x read by TMA as FP32,
+// 16-byte aligned rows and pitch: gemm_fused_ok); only the row exponents
+// come from `work`, written by gemm_rowpow_launch.
 cudaError_t gemm_mul_launch(int64_t batch, int64_t n, int64_t m, int terms, const void* z, const void* work,
                             float2* X, int64_t ld_X, unsigned* status, int sms, uint64_t timeout_ns,
-                            cudaStream_t st, const int* col_pow = nullptr);
+                            cudaStream_t st, const int* col_pow = nullptr, const float* x = nullptr,
+                            int64_t ld_x = 0);
+bool gemm_fused_ok(const float* x, int64_t ld_x);
+cudaError_t gemm_rowpow_launch(const float* x, int64_t batch, int64_t n, int64_t ld_x, void* work, cudaStream_t st);
 // Z off the unit circle; col_pow (device, M ints): log2 of each column's scale.
 cudaError_t gemm_build_z_spiral(int64_t n, int64_t m, uint64_t A, uint64_t B, double la, double lw,
                                 const int* col_pow, void* z, cudaStream_t st);

@@ -267,3 +267,20 @@ def test_gemm_output_pitch_and_edges(ctx, S, batch, m, ld):
     assert rel(got[:, :m], O.czt(x, FS, 0.3e12, 2.2e12, m)).max() <= TOL
     if ld > m:
         assert np.isnan(got[:, m:].real).all() and np.isnan(got[:, m:].imag).all()
+
+
+def test_gemm_with_the_split_inside_the_product(S, monkeypatch):
+    # SPEC_GEMM_FUSED=1: x is read as FP32 boxes by TMA and split into the FP16
+    # parts by converter warps inside the product; the parts are the same bits
+    # as the separate split pass's, so the spectra are identical
+    x = dev(noise(300, 1000, 77))
+    with S.Context(0) as c0:
+        ref = S.spec_czt(c0, x, FS, 0.3e12, 2.2e12, 256, mode=S.SPEC_CZT_GEMM_F16X3)
+        ref1 = S.spec_czt(c0, x, FS, 0.3e12, 2.2e12, 256, mode=S.SPEC_CZT_GEMM_BF16X1)
+    monkeypatch.setenv("SPEC_GEMM_FUSED", "1")
+    with S.Context(0) as c1:
+        got = S.spec_czt(c1, x, FS, 0.3e12, 2.2e12, 256, mode=S.SPEC_CZT_GEMM_F16X3)
+        got1 = S.spec_czt(c1, x, FS, 0.3e12, 2.2e12, 256, mode=S.SPEC_CZT_GEMM_BF16X1)
+    assert torch.equal(torch.view_as_real(got), torch.view_as_real(ref))
+    assert torch.equal(torch.view_as_real(got1), torch.view_as_real(ref1))
+    assert rel(got.cpu().numpy(), O.czt(x.cpu().numpy(), FS, 0.3e12, 2.2e12, 256)).max() <= TOL
