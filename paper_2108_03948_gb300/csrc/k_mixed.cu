@@ -196,6 +196,174 @@ __global__ void __launch_bounds__(kMixedCta) k_fft_mixed(MixedArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident form for residue lengths 250, 500 and 1000 (LZ = 10 x
+// 5 x 5, 10 x 10 x 5, 10 x 10 x 10: the residue DFTs of the paper's N = 500
+// traces and of 1000 / 2000-sample ones).  Each residue DFT runs on T = LZ/10
+// threads holding 10 elements each in registers (t + T i before and after
+// the transform, as BlockFFT does for powers of two): Stockham passes of
+// radix 10 (two radix-5 DFTs and a radix-2 combination) and 5, each followed
+// by one exchange through the residue's shared-memory area, with the pass
+// twiddles from the plan's table.  Residues are padded to LZ + 1 values, so
+// the unpack's reads of Z[k] for consecutive k (consecutive residues) fall on
+// different banks.
+template <int LZ> struct MixedRegShape;
+template <> struct MixedRegShape<250> {
+    static constexpr int rad(int p) { return p == 0 ? 10 : 5; }
+};
+template <> struct MixedRegShape<500> {
+    static constexpr int rad(int p) { return p < 2 ? 10 : 5; }
+};
+template <> struct MixedRegShape<1000> {
+    static constexpr int rad(int p) { return 10; }
+};
+
+template <int LZ> __host__ __device__ constexpr int mreg_ns(int p) {
+    return p == 0 ? 1 : mreg_ns<LZ>(p - 1) * MixedRegShape<LZ>::rad(p - 1);
+}
+// offset of pass p's twiddles in the plan's pass table (passes with NS > 1)
+template <int LZ> __host__ __device__ constexpr int mreg_twoff(int p) {
+    return p <= 1 ? 0 : mreg_twoff<LZ>(p - 1) + (MixedRegShape<LZ>::rad(p - 1) - 1) * mreg_ns<LZ>(p - 1);
+}
+
+__device__ __forceinline__ void dft5(float2* v) {
+    float2 w[8] = {v[0], v[1], v[2], v[3], v[4]};
+    dft_odd<5>(w);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = w[i];
+}
+
+// 10 = 2 x 5: X[k] = E[k] + w10^k O[k], X[k + 5] = E[k] - w10^k O[k]
+__device__ __forceinline__ void dft10(float2 (&v)[10]) {
+    float2 e[5] = {v[0], v[2], v[4], v[6], v[8]};
+    float2 o[5] = {v[1], v[3], v[5], v[7], v[9]};
+    dft5(e);
+    dft5(o);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        // w10^k = e^{-j pi k/5} = e^{-j pi (32 k/5)/32}: cos(pi k/5), -sin(pi k/5)
+        const float c = k == 0 ? 1.f : k == 1 ? 0.80901699437494742f : k == 2 ? 0.30901699437494742f
+                      : k == 3 ? -0.30901699437494742f : -0.80901699437494742f;
+        const float sn = k == 0 ? 0.f : (k == 1 || k == 4) ? 0.58778525229247313f : 0.95105651629515357f;
+        const float2 t = make_float2(fmaf(o[k].x, c, o[k].y * sn), fmaf(o[k].y, c, -o[k].x * sn));
+        v[k] = cadd(e[k], t);
+        v[k + 5] = csub(e[k], t);
+    }
+}
+
+template <int LZ, int P>
+__device__ __forceinline__ void mreg_compute(float2 (&v)[10], int t, const float2* tw) {
+    constexpr int T = LZ / 10;
+    constexpr int RP = MixedRegShape<LZ>::rad(P);
+    constexpr int NS = mreg_ns<LZ>(P);
+    constexpr int NB = 10 / RP;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        float2 u[10];
+#pragma unroll
+        for (int r = 0; r < RP; ++r) u[r] = v[b + r * NB];
+        if constexpr (NS > 1) {
+            const int k = (t + T * b) % NS;
+            const float2* twp = tw + mreg_twoff<LZ>(P) + k;
+#pragma unroll
+            for (int r = 1; r < RP; ++r) u[r] = cmul(u[r], __ldg(twp + (r - 1) * NS));
+        }
+        if constexpr (RP == 10) dft10(u);
+        else dft5(u);
+#pragma unroll
+        for (int r = 0; r < RP; ++r) v[b + r * NB] = u[r];
+    }
+}
+
+// the outputs of pass P to their Stockham positions, then the thread's next
+// inputs t + T i
+template <int LZ, int P>
+__device__ __forceinline__ void mreg_exchange(float2 (&v)[10], float2* s, int t) {
+    constexpr int T = LZ / 10;
+    constexpr int RP = MixedRegShape<LZ>::rad(P);
+    constexpr int NS = mreg_ns<LZ>(P);
+    constexpr int NB = 10 / RP;
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = t + T * b;
+        const int k = j % NS;
+        const int base = (j - k) * RP + k;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) s[base + r * NS] = v[b + r * NB];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 10; ++i) v[i] = s[t + T * i];
+}
+
+struct MixedRegArgs {
+    const float* x;
+    int64_t batch;
+    int n;
+    int64_t ld_x;
+    float2* X;
+    int64_t ld_X;
+    int H, R, F;
+    float rR;
+    const float2* tab;
+    int pre_off, pass_off, unpack_off;
+};
+
+template <int LZ>
+__global__ void __launch_bounds__(1000) k_fft_mixed_regs(MixedRegArgs a) {
+    constexpr int E = 10, T = LZ / E, LZP = LZ + 1;
+    static_assert(mreg_ns<LZ>(3) == LZ, "three passes of the shape cover LZ");
+    extern __shared__ float2 smem[];
+    const int R = a.R, H = a.H;
+    const int PT = R * T;                            // threads per trace
+    const int f = threadIdx.x / PT;
+    const int lt = threadIdx.x - f * PT;
+    const int res = lt / T;
+    const int t = lt - res * T;
+    const int64_t b = (int64_t)blockIdx.x * a.F + f;
+    const bool live = b < a.batch;
+    float2* zs = smem + (size_t)f * R * LZP;
+    float2* s = zs + res * LZP;
+    // 1-2. packed, pre-twiddled input of this thread's residue: m = t + T i
+    float2 v[E];
+    {
+        const float* xr = a.x + (live ? b : 0) * a.ld_x;
+        const float2* pre = a.tab + a.pre_off + res * LZ;
+        const int n = a.n;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            const float re = live && 2 * m < n ? __ldg(xr + 2 * m) : 0.f;
+            const float im = live && 2 * m + 1 < n ? __ldg(xr + 2 * m + 1) : 0.f;
+            v[i] = cmul(make_float2(re, im), __ldg(pre + m));
+        }
+    }
+    // 3. the residue DFT: three passes in registers
+    const float2* tw = a.tab + a.pass_off;
+    mreg_compute<LZ, 0>(v, t, tw);
+    mreg_exchange<LZ, 0>(v, s, t);
+    mreg_compute<LZ, 1>(v, t, tw);
+    mreg_exchange<LZ, 1>(v, s, t);
+    mreg_compute<LZ, 2>(v, t, tw);
+    // Z[R q + res] at q = t + T i
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E; ++i) s[t + T * i] = v[i];
+    __syncthreads();
+    if (!live) return;
+    // 4. unpack the pairs (k, H - k); Z[k] = zs[(k mod R) LZP + k / R]
+    float2* Xr = a.X + b * a.ld_X;
+    const float2* wk = a.tab + a.unpack_off;
+    for (int k = lt; k <= H / 2; k += PT) {
+        const int km = k == 0 ? 0 : H - k;
+        int ra, rb;
+        const int qa = fdivmod(k, R, a.rR, &ra);
+        const int qb = fdivmod(km, R, a.rR, &rb);
+        unpack_pair_mixed(Xr, k, H, zs[ra * LZP + qa], zs[rb * LZP + qb], __ldg(wk + k));
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------- host --
@@ -234,6 +402,14 @@ bool mixed_plan(int64_t n, int64_t n_fft, MixedPlan* p, std::string* why) {
         p->LZ = (int)LZ;
         p->R = (int)(H / LZ);
         p->radix = rad;
+        // residue lengths with a register-resident kernel (one CTA of at most
+        // 1000 threads per trace): its radix plan sets the table layout
+        if ((LZ == 250 || LZ == 500 || LZ == 1000) && p->R * (LZ / 10) <= 1000) {
+            p->regs = true;
+            p->radix = LZ == 250 ? std::vector<int>{10, 5, 5}
+                     : LZ == 500 ? std::vector<int>{10, 10, 5} : std::vector<int>{10, 10, 10};
+        }
+        rad = p->radix;
         // table: pre-twiddles [R][LZ] | pass twiddles | unpack
         int pass = 0, ns = 1;
         for (int r : rad) {
@@ -272,9 +448,33 @@ void mixed_fill_table(const MixedPlan& p, float2* host) {
     for (int64_t k = 0; k <= H / 2; ++k) host[p.unpack_off + k] = w(k, 2 * H);
 }
 
+static cudaError_t mixed_regs_launch(const MixedPlan& p, const float* x, int64_t batch, int n, int64_t ld_x,
+                                     const float2* tab, float2* X, int64_t ld_X, cudaStream_t st) {
+    MixedRegArgs a = {};
+    a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x; a.X = X; a.ld_X = ld_X;
+    a.H = p.H; a.R = p.R; a.rR = 1.0f / (float)p.R;
+    a.tab = tab; a.pre_off = p.pre_off; a.pass_off = p.pass_off; a.unpack_off = p.unpack_off;
+    const int PT = p.R * (p.LZ / 10);
+    const size_t per = (size_t)p.R * (p.LZ + 1) * sizeof(float2);
+    int F = std::max(1, 1000 / PT);
+    while (F > 1 && (size_t)F * per > 100 * 1024) --F;
+    a.F = F;
+    const size_t smem = (size_t)F * per;
+    const void* k = p.LZ == 250 ? (const void*)k_fft_mixed_regs<250>
+                  : p.LZ == 500 ? (const void*)k_fft_mixed_regs<500> : (const void*)k_fft_mixed_regs<1000>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((batch + F - 1) / F);
+    if (p.LZ == 250) k_fft_mixed_regs<250><<<grid, F * PT, smem, st>>>(a);
+    else if (p.LZ == 500) k_fft_mixed_regs<500><<<grid, F * PT, smem, st>>>(a);
+    else k_fft_mixed_regs<1000><<<grid, F * PT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t mixed_launch(const MixedPlan& p, const float* x, int64_t batch, int n, int64_t ld_x, const float2* tab,
                          float2* X, int64_t ld_X, cudaStream_t st) {
     if (batch == 0) return cudaSuccess;
+    if (p.regs) return mixed_regs_launch(p, x, batch, n, ld_x, tab, X, ld_X, st);
     MixedArgs a = {};
     a.x = x; a.batch = batch; a.n = n; a.ld_x = ld_x; a.X = X; a.ld_X = ld_X;
     a.H = p.H; a.LZ = p.LZ; a.R = p.R; a.npass = (int)p.radix.size();

@@ -113,6 +113,7 @@ constexpr int64_t kMixedMaxH = 13312;     // 2 H complex values within one CTA's
 struct MixedPlan {
     int H = 0, LZ = 0, R = 0;
     std::vector<int> radix;               // Stockham passes of the LZ-point DFT
+    bool regs = false;                    // LZ 250 / 500 / 1000: the register-resident kernel (radix 10, 5)
     int pre_off = 0, pass_off = 0, root_off = 0, unpack_off = 0, entries = 0;
     size_t smem = 0;
 };
