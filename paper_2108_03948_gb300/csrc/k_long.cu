@@ -107,8 +107,13 @@ struct ColArgs {
     float2* W;                       // [batch][P1][P2]
 };
 
+// Two CTAs per SM up to 1024-point columns: at 64 registers the 512- and
+// 1024-point forms spill ~150 bytes, yet the passes wait mostly on global
+// loads and twice the warps hide more of it (measured on a 2^19-point
+// Bluestein of 256 traces: 2.37 ms per call at one CTA per SM, 1.88 ms with
+// this pass and the inverse column pass at two).
 template <int LZ1>
-__global__ void __launch_bounds__(512, LZ1 >= 512 ? 1 : 2) k_long_cols(ColArgs a) {
+__global__ void __launch_bounds__(512, LZ1 >= 2048 ? 1 : 2) k_long_cols(ColArgs a) {
     using FFT = BlockFFT<LZ1, false>;
     constexpr int E = FFT::E, T = FFT::T;
     extern __shared__ float2 smem[];
@@ -290,7 +295,7 @@ struct ColInvArgs {
 };
 
 template <int P1>
-__global__ void __launch_bounds__(512, P1 >= 512 ? 1 : 2) k_long_cols_inv(ColInvArgs a) {
+__global__ void __launch_bounds__(512, P1 >= 2048 ? 1 : 2) k_long_cols_inv(ColInvArgs a) {
     using Iv = BlockFFT<P1, true>;
     constexpr int E = Iv::E, T = Iv::T;
     extern __shared__ float2 smem[];
