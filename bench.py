@@ -154,21 +154,23 @@ def host_link_gbs(dev, nbytes=256 << 20, reps=5):
 
 
 # Kernel sources behind each transform's timed launches: stored traffic
-# counters stay valid while these files are unchanged.
+# counters stay valid while these files are unchanged.  The multi-pass
+# kernels (k_long.cu) run only at workload 4, the ragged plan only at 2.
 DIGEST_SOURCES = {
-    "fft": ["k_fft.cu", "k_long.cu", "fft_block.cuh", "mbarrier.cuh", "spec_internal.h"],
-    "czt": ["k_czt.cu", "k_gemm.cu", "k_long.cu", "fft_block.cuh", "mbarrier.cuh", "spec_internal.h"],
+    "fft": ["k_fft.cu", "fft_block.cuh", "mbarrier.cuh", "spec_internal.h"],
+    "czt": ["k_czt.cu", "k_gemm.cu", "fft_block.cuh", "mbarrier.cuh", "spec_internal.h"],
     "zoom": ["k_zoom.cu", "k_fft.cu", "fft_block.cuh", "spec_internal.h"],
 }
+DIGEST_EXTRA = {2: ["ragged.cu"], 4: ["k_long.cu"]}
 
 
 def csrc_digest(kernel, workload=None):
-    """Digest of the kernel sources of one transform (plus the ragged plan for
-    workload 2): stored traffic counters are valid only for those sources."""
+    """Digest of the kernel sources of one transform at one workload:
+    stored traffic counters are valid only for those sources."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2108_03948_gb300", "csrc")
-    names = list(DIGEST_SOURCES[kernel]) + (["ragged.cu"] if workload == 2 else [])
+    names = list(DIGEST_SOURCES[kernel]) + DIGEST_EXTRA.get(workload, [])
     for name in sorted(names):
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
