@@ -73,9 +73,11 @@ struct BluesteinArgs {
 };
 
 // Up to L = 4096: 256 threads (one or more traces) at four CTAs per SM, i.e.
-// 64 registers, which this kernel fits without spills.
+// 64 registers, which this kernel fits without spills; L = 8192: 512 threads
+// at two CTAs per SM (64 registers, no spills; 68 KB of shared memory each).
 template <int L>
-__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256, FFTShape<L>::T > 256 ? 1 : 4) k_czt_bluestein(BluesteinArgs a) {
+__global__ void __launch_bounds__(FFTShape<L>::T > 256 ? FFTShape<L>::T : 256,
+                                  FFTShape<L>::T > 512 ? 1 : FFTShape<L>::T > 256 ? 2 : 4) k_czt_bluestein(BluesteinArgs a) {
     using Fw = BlockFFT<L, false>;
     using Iv = BlockFFT<L, true>;
     constexpr int E = Fw::E, T = Fw::T;
