@@ -462,6 +462,16 @@ __device__ __forceinline__ C2 pretwiddle2(float2 z, float4 w) {
     const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
     return C2{sub2(mul2(zx, wr), mul2(zy, wi)), fma2(zx, wi, mul2(zy, wr))};
 }
+// Folded input of two residues (lanes a, b): (z0 + z1 c_lane) w_lane, with
+// c = (ca.x, cb.x, ca.y, cb.y) and w packed the same way
+__device__ __forceinline__ C2 pretwiddle2_fold(float2 z0, float2 z1, float4 c, float4 w) {
+    const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
+    const float2 z1x = make_float2(z1.x, z1.x), z1y = make_float2(z1.y, z1.y);
+    const float2 zx = fma2(z1x, cr, fma2(make_float2(-z1.y, -z1.y), ci, make_float2(z0.x, z0.x)));
+    const float2 zy = fma2(z1x, ci, fma2(z1y, cr, make_float2(z0.y, z0.y)));
+    const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+    return C2{sub2(mul2(zx, wr), mul2(zy, wi)), fma2(zx, wi, mul2(zy, wr))};
+}
 
 // X[k], X[H - k] from A = Z[k], B = Z[H - k], w = e^{-j pi k/H}/2 (the 1/2
 // of the real-input unpack folded into w), 0 < k < H/2
@@ -596,10 +606,27 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_padded2r(FftArgs a) {
 // traffic costing more than the register moves it saves).  The per-k
 // twiddles are ub4 and um times compile-time constants (k = lt + PT j:
 // w_{2H}^{PT j} = e^{-j pi j/32}, w_LZ^{(PT/R) j} = e^{-j 2 pi j/32}).
-__host__ __device__ constexpr int fused_ub4_index(int LZ, int R) { return (R / 2) * LZ; }
-__host__ __device__ constexpr int fused_um_index(int LZ, int R) { return 2 * (fused_ub4_index(LZ, R) + (R / 2) * (LZ / 16)); }
-__host__ __device__ constexpr int fused_tw2_index(int LZ, int R) { return fused_um_index(LZ, R) + (R / 2) * (LZ / 16); }
-__host__ __device__ constexpr int fused_entries(int LZ, int R) { return fused_tw2_index(LZ, R) + fft_twiddle_entries(LZ); }
+//
+// Folded form (FOLD = 2): traces of up to 2 LZ sample pairs with R = H/LZ
+// residues of LZ points, z[m0] and z[m0 + LZ] summed before the residue FFT:
+//   Z[R q + r] = sum_{m0 < LZ} w_H^{m0 r} (z[m0] + z[m0 + LZ] w_R^r) w_LZ^{m0 q}
+// (w_H^{LZ r} = w_R^r, w_H^{LZ R q} = 1).  This lets a trace of 2 LZ pairs
+// use the kernel of LZ-point residues (LZ = 512: radix 16, 16, 2, each pair
+// of residues one warp) instead of 2 LZ-point ones.  The table then holds,
+// after pre4, fold4 [R/2] = (w_R^{2p}, w_R^{2p+1}) packed like pre4.
+__host__ __device__ constexpr int fused_fold4_index(int LZ, int R) { return (R / 2) * LZ; }
+__host__ __device__ constexpr int fused_ub4_index(int LZ, int R, int FOLD = 1) {
+    return (R / 2) * LZ + (FOLD > 1 ? R / 2 : 0);
+}
+__host__ __device__ constexpr int fused_um_index(int LZ, int R, int FOLD = 1) {
+    return 2 * (fused_ub4_index(LZ, R, FOLD) + (R / 2) * (LZ / 16));
+}
+__host__ __device__ constexpr int fused_tw2_index(int LZ, int R, int FOLD = 1) {
+    return fused_um_index(LZ, R, FOLD) + (R / 2) * (LZ / 16);
+}
+__host__ __device__ constexpr int fused_entries(int LZ, int R, int FOLD = 1) {
+    return fused_tw2_index(LZ, R, FOLD) + fft_twiddle_entries(LZ);
+}
 // float2 per trace: the BlockFFT exchange areas of the R/2 pairs (the staged
 // H values fit in the same space)
 __host__ __device__ constexpr int fused_trace_smem(int LZ, int R) { return (R / 2) * padded_len(LZ) * 2; }
@@ -629,7 +656,7 @@ __device__ __forceinline__ void fused_butterfly(float2 (&y)[RHO], float2 w) {
 // __syncthreads); threads of a trace slot without a trace pass live = false.
 // (bar, nthr): the trace's barrier (group_sync); pbar: the barrier of the
 // residue pair's exchange (-1: the pair is one warp), 64 threads.
-template <int LZ, int R>
+template <int LZ, int R, int FOLD = 1>
 __device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl, int t, int lt, bool live,
                                                  float2* Xr, const float2* tab, int bar, int nthr, int pbar) {
     using S = FFTShape<LZ, 16>;
@@ -647,7 +674,7 @@ __device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl
     using FFT = BlockFFT<LZ, false, C2, 16, float2>;
     // the exchange between passes 0 and 1 touches only the pair's own area
     FFT::template run_first<2>(v, reinterpret_cast<float4*>(zs) + gl * padded_len(LZ), t,
-                               tab + fused_tw2_index(LZ, R), pbar, T);
+                               tab + fused_tw2_index(LZ, R, FOLD), pbar, T);
 
     // outputs of pass 1 (radix 16, span 16): v[r] is position base + 16 r of
     // residues 2 gl and 2 gl + 1, staged at x = pos R + 2 gl
@@ -665,10 +692,10 @@ __device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl
     group_sync(bar, nthr);
     if (!live) return;
 
-    const float4 ub = __ldg(tab4 + fused_ub4_index(LZ, R) + lt);
+    const float4 ub = __ldg(tab4 + fused_ub4_index(LZ, R, FOLD) + lt);
     const float2 wk0 = make_float2(ub.x, ub.y);    // w_{2H}^{lt} / 2
     const float2 wq0 = make_float2(ub.z, ub.w);    // w_LZ^{lt/R}
-    const float2 wm0 = __ldg(tab + fused_um_index(LZ, R) + lt);
+    const float2 wm0 = __ldg(tab + fused_um_index(LZ, R, FOLD) + lt);
     // the swizzle depends only on the low 7 bits of x, and PT j, m HB are
     // multiples of 128: every slot below is a base plus a constant
     const float2* zf = zs + fsw(lt);
@@ -716,7 +743,7 @@ __device__ __forceinline__ void fused_fft_unpack(C2 (&v)[16], float2* zs, int gl
     }
 }
 
-template <int LZ, int R>
+template <int LZ, int R, int FOLD = 1>
 __global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
     constexpr int T = LZ / 16, E = 16, G = R / 2, PT = G * T;
     constexpr int F = PT >= 256 ? 1 : 256 / PT;
@@ -741,26 +768,48 @@ __global__ void __launch_bounds__(256, 2) k_fft_real_fused(FftArgs a) {
     const float4* w4 = reinterpret_cast<const float4*>(a.tab) + gl * LZ + t;
     C2 v[E];
     const float* xr = a.x + xo;
-    if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
-        const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
+    if constexpr (FOLD == 1) {
+        if (live && n >= 2 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
+            const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = pretwiddle2(__ldg(x2 + T * i), __ldg(w4 + T * i));
+            for (int i = 0; i < E; ++i) v[i] = pretwiddle2(__ldg(x2 + T * i), __ldg(w4 + T * i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int m = t + T * i;
+                float re = 0.f, im = 0.f;
+                if (live && 2 * m < n) re = __ldg(xr + 2 * m);
+                if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
+                v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
+            }
+        }
     } else {
+        static_assert(FOLD == 2, "fold of two");
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(a.tab) + fused_fold4_index(LZ, R) + gl);
+        if (live && n >= 4 * LZ && (reinterpret_cast<uintptr_t>(xr) & 7) == 0) {
+            const float2* x2 = reinterpret_cast<const float2*>(xr) + t;
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int m = t + T * i;
-            float re = 0.f, im = 0.f;
-            if (live && 2 * m < n) re = __ldg(xr + 2 * m);
-            if (live && 2 * m + 1 < n) im = __ldg(xr + 2 * m + 1);
-            v[i] = pretwiddle2(make_float2(re, im), __ldg(w4 + T * i));
+            for (int i = 0; i < E; ++i)
+                v[i] = pretwiddle2_fold(__ldg(x2 + T * i), __ldg(x2 + LZ + T * i), c4, __ldg(w4 + T * i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int m = t + T * i, m1 = m + LZ;
+                float2 z0 = make_float2(0.f, 0.f), z1 = make_float2(0.f, 0.f);
+                if (live && 2 * m < n) z0.x = __ldg(xr + 2 * m);
+                if (live && 2 * m + 1 < n) z0.y = __ldg(xr + 2 * m + 1);
+                if (live && 2 * m1 < n) z1.x = __ldg(xr + 2 * m1);
+                if (live && 2 * m1 + 1 < n) z1.y = __ldg(xr + 2 * m1 + 1);
+                v[i] = pretwiddle2_fold(z0, z1, c4, __ldg(w4 + T * i));
+            }
         }
     }
     // F > 1: each trace's threads synchronise on their own named barrier;
     // each residue pair's exchange on its warp (T = 32) or on a named
     // barrier of its two warps (ids after the traces')
     static_assert(T == 32 || (T == 64 && F + F * G < 8), "barrier ids");
-    fused_fft_unpack<LZ, R>(v, reinterpret_cast<float2*>(smem4) + f * TS, gl, t, lt, live, a.X + Xo, a.tab,
-                            F > 1 ? 1 + f : 0, PT, T == 32 ? -1 : 1 + F + f * G + gl);
+    fused_fft_unpack<LZ, R, FOLD>(v, reinterpret_cast<float2*>(smem4) + f * TS, gl, t, lt, live, a.X + Xo,
+                                  a.tab, F > 1 ? 1 + f : 0, PT, T == 32 ? -1 : 1 + F + f * G + gl);
 }
 
 // Persistent form for whole rows at 16-byte aligned addresses (n = 2 LZ,
@@ -1522,13 +1571,21 @@ static FftKernel fft_kernel_fixed_for(int LZ, int R) {
 
 // (LZ, R) pairs with a compiled fused-unpack kernel (three-pass BlockFFT,
 // R/2 LZ/16 threads per trace a multiple of 128)
-static FftKernel fft_kernel_fused_for(int LZ, int R, bool tma = false) {
+static FftKernel fft_kernel_fused_for(int LZ, int R, bool tma = false, int fold = 1) {
+    if (fold == 2) {
+        // folded input (traces of up to 2 LZ sample pairs), plain grid only
+        if (tma) return nullptr;
+        if (LZ == 512 && R == 8) return k_fft_real_fused<512, 8, 2>;
+        if (LZ == 512 && R == 16) return k_fft_real_fused<512, 16, 2>;
+        return nullptr;
+    }
+    if (fold != 1) return nullptr;
 #define SPEC_FUSED(lz, r) if (LZ == lz && R == r) return tma ? k_fft_real_fused_tma<lz, r> : k_fft_real_fused<lz, r>;
     SPEC_FUSED(512, 8) SPEC_FUSED(512, 16) SPEC_FUSED(1024, 4) SPEC_FUSED(1024, 8)
 #undef SPEC_FUSED
     return nullptr;
 }
-bool fft_fused_available(int LZ, int R) { return fft_kernel_fused_for(LZ, R) != nullptr; }
+bool fft_fused_available(int LZ, int R, int fold) { return fft_kernel_fused_for(LZ, R, false, fold) != nullptr; }
 
 // (LZ, R) pairs with a compiled cluster kernel (one trace per cluster of
 // R LZ/8192 CTAs)
@@ -1654,7 +1711,7 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 
 int fft_table_entries(const FftPlan& p) {
     if (p.clustered) return 2 * (cluster_tw4_index(p.H) + fft_twiddle_entries(p.LZ));
-    if (p.fused) return fused_entries(p.LZ, p.R);
+    if (p.fused) return fused_entries(p.LZ, p.R, p.fold);
     const int generic = p.R * p.T + p.R * p.E + p.H / 2 + 1;
     if (!p.fixed) return generic;
     // + packed pre-twiddles [R/2][LZ] and BlockFFT<LZ> twiddles, float4 each
@@ -1705,13 +1762,21 @@ void fft_fill_table(const FftPlan& p, float2* host) {
             // BlockFFT<LZ> twiddles as (c, s): the packed form, then repacked
             std::vector<float4> t4tw((size_t)fft_twiddle_entries(p.LZ));
             tw4_fill(t4tw.data());
-            float2* d2 = host + fused_tw2_index(p.LZ, p.R);
+            float2* d2 = host + fused_tw2_index(p.LZ, p.R, p.fold);
             for (size_t e = 0; e < t4tw.size(); ++e) d2[e] = make_float2(t4tw[e].x, t4tw[e].z);
         }
         const int PT = (p.R / 2) * (p.LZ / 16);
         const int NS = p.LZ / (1 << (ilog2(p.LZ) % 4));  // span of the fused last pass
-        float4* ub = t4 + fused_ub4_index(p.LZ, p.R);
-        float2* um = host + fused_um_index(p.LZ, p.R);
+        if (p.fold == 2) {
+            // fold4: w_R^{2g}, w_R^{2g+1} (= w_H^{LZ r}), packed like pre4
+            float4* f4 = t4 + fused_fold4_index(p.LZ, p.R);
+            for (int g = 0; g < p.R / 2; ++g) {
+                const float2 ca = w(2 * g, p.R), cb = w(2 * g + 1, p.R);
+                f4[g] = make_float4(ca.x, cb.x, ca.y, cb.y);
+            }
+        }
+        float4* ub = t4 + fused_ub4_index(p.LZ, p.R, p.fold);
+        float2* um = host + fused_um_index(p.LZ, p.R, p.fold);
         for (int lt = 0; lt < PT; ++lt) {
             const int r = lt % p.R, q0 = lt / p.R;
             const float2 wk = w(lt, 2 * H), wq = w(q0, p.LZ);
@@ -1738,7 +1803,7 @@ void fft_fill_table(const FftPlan& p, float2* host) {
 }
 
 bool fft_fused_tma_ok(const FftPlan& p, const float* x, int n, int64_t ld_x) {
-    return p.fused && fft_kernel_fused_for(p.LZ, p.R, true) != nullptr && n == 2 * p.LZ &&
+    return p.fused && p.fold == 1 && fft_kernel_fused_for(p.LZ, p.R, true) != nullptr && n == 2 * p.LZ &&
            (reinterpret_cast<uintptr_t>(x) & 15) == 0 && (ld_x & 3) == 0;
 }
 
@@ -1797,7 +1862,7 @@ cudaError_t fft_launch(const FftPlan& p, const float* x, int64_t batch, int n, i
     }
     const bool dual = p.dual && lanes != 1;
     if (dual && p.fused) {
-        FftKernel kf = fft_kernel_fused_for(p.LZ, p.R);
+        FftKernel kf = fft_kernel_fused_for(p.LZ, p.R, false, p.fold);
         if (!kf) return cudaErrorInvalidValue;
         const int PT = (p.R / 2) * (p.LZ / 16);
         const int F = std::max(1, 256 / PT);

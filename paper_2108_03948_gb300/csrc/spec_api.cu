@@ -249,7 +249,7 @@ spec_status check_common(spec_ctx* c, const float* x, int64_t batch, int64_t n, 
 
 int table_layout(int kind, const FftPlan& p) {
     if (kind != 0) return 0;
-    return p.clustered ? 2 : p.fused ? 3 : p.fixed ? 1 : 0;
+    return p.clustered ? 2 : p.fused ? (p.fold == 2 ? 4 : 3) : p.fixed ? 1 : 0;
 }
 
 // Per-shape twiddle tables of the padded real FFT (kind 0) and of the pruned
@@ -676,6 +676,19 @@ spec_status spec_fft(spec_ctx* c, const float* x, int64_t batch, int64_t n, int6
                     vars.push_back({q, 4});
                     names.push_back("fusedp");
                 }
+            }
+            if (fft_fused_available(p.LZ / 2, 2 * p.R, 2)) {
+                // residues of LZ/2 points on folded input (k_fft_real_fused, FOLD = 2)
+                q = p;
+                q.fixed = false;
+                q.fused = true;
+                q.fold = 2;
+                q.LZ = p.LZ / 2;
+                q.R = 2 * p.R;
+                q.Rc = q.R;
+                q.T = q.LZ / 16;
+                vars.push_back({q, 0});
+                names.push_back("fold");
             }
         }
         if (p.dual || p.fixed) {

@@ -58,6 +58,7 @@ struct FftPlan {
     bool fixed = false;   // two-lane kernel compiled for this (LZ, R) with packed tables (C == 1)
     bool clustered = false;  // one cluster of C CTAs per trace, conjugate-paired residues (k_fft_real_cluster)
     bool fused = false;      // fixed two-lane kernel with the last pass fused into the unpack (k_fft_real_fused)
+    int fold = 1;            // fused: sample pairs m and m + LZ summed into one residue input (1 or 2)
     int emax = 16;      // elements per thread (16 or 32: radix of the passes)
     int trace_smem = 0; // float2 of shared memory per trace per CTA
     int threads = 0;
@@ -73,8 +74,8 @@ bool fft_plan(int64_t batch, int64_t n, int64_t n_fft, FftPlan* p, std::string* 
 // `fixed` also the packed two-lane pre-twiddles and BlockFFT twiddles),
 // float64 on the host, rounded to float.
 int fft_table_entries(const FftPlan& p);
-// true if k_fft_real_fused has an instance for (LZ, R)
-bool fft_fused_available(int LZ, int R);
+// true if k_fft_real_fused has an instance for (LZ, R) and the fold (1 or 2)
+bool fft_fused_available(int LZ, int R, int fold = 1);
 // The persistent fused kernel that prefetches rows with bulk copies: whole
 // rows (n = 2 LZ) at 16-byte aligned addresses and pitch only.
 bool fft_fused_tma_ok(const FftPlan& p, const float* x, int n, int64_t ld_x);

@@ -33,8 +33,11 @@ def fsw(x):
 
 def residue_partials(z, r, H, LZ, rho):
     """Outputs of the first two passes of residue r in Stockham order: the
-    NS-point DFTs of the decimated, pre-twiddled input, a[j + m NS]."""
+    NS-point DFTs of the decimated, pre-twiddled input, a[j + m NS].  A z
+    longer than LZ is folded first: z[m0] + z[m0 + LZ] w_R^r (R = H/LZ)."""
     NS = LZ // rho
+    if len(z) > LZ:
+        z = z[:LZ] + z[LZ:] * w(r, H // LZ)
     v = z * w(r * np.arange(LZ), H)
     a = np.zeros(LZ, complex)
     for m in range(rho):
@@ -52,14 +55,14 @@ def bank_ways(words, width):
     return max(len(v) for v in banks.values())
 
 
-def fused_model(LZ, R, seed, plant=None):
+def fused_model(LZ, R, seed, plant=None, fold=1):
     H = R * LZ
     rho = 1 << (int(np.log2(LZ)) % 4)
     NS, HB, J = LZ // rho, H // rho, 16 // rho
     T, G = LZ // 16, R // 2
     PT = G * T
     rng = np.random.default_rng(seed)
-    x = rng.standard_normal(2 * LZ)
+    x = rng.standard_normal(2 * LZ * fold)
     z = x[0::2] + 1j * x[1::2]
     parts = {r: residue_partials(z, r, H, LZ, rho) for r in range(R)}
 
@@ -138,6 +141,30 @@ def test_fused_layout_reproduces_the_padded_fft(LZ, R):
     assert np.abs(X - ref).max() <= 1e-12 * np.abs(ref).max()
     assert st == 1 and fwd == 1
     assert mir <= 2
+
+
+@pytest.mark.parametrize("LZ,R", [(512, 8), (512, 16)])
+def test_folded_input_reproduces_the_padded_fft(LZ, R):
+    # the folded form: traces of 2 LZ sample pairs through LZ-point residues,
+    # z[m0] + z[m0 + LZ] w_R^r summed before the pre-twiddle
+    x, X, count, _ = fused_model(LZ, R, seed=7 * LZ + R, fold=2)
+    assert (count == 1).all()
+    ref = np.fft.rfft(x, 2 * R * LZ)
+    assert np.abs(X - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_planted_fold_twiddle_is_caught():
+    # the fold twiddle w_R^r taken with the wrong sign must break the spectrum
+    LZ, R = 512, 16
+    rng = np.random.default_rng(11)
+    z = rng.standard_normal(2 * LZ) + 1j * rng.standard_normal(2 * LZ)
+    H = R * LZ
+    Z = np.fft.fft(z, H)
+    r = 3
+    good = np.fft.fft((z[:LZ] + z[LZ:] * w(r, R)) * w(r * np.arange(LZ), H))
+    bad = np.fft.fft((z[:LZ] + z[LZ:] * np.conj(w(r, R))) * w(r * np.arange(LZ), H))
+    assert np.allclose(good, Z[r::R], rtol=0, atol=1e-9 * np.abs(Z).max())
+    assert not np.allclose(bad, Z[r::R], rtol=0, atol=1e-3 * np.abs(Z).max())
 
 
 @pytest.mark.parametrize("plant", ["mirror", "twiddle"])

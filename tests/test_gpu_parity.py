@@ -333,7 +333,7 @@ VARIANT_CASES = [(5, 1024, 8192), (3, 1000, 8192), (3, 513, 8192),      # LZ 512
                  (4, 2048, 16384), (3, 1025, 16384)]                     # LZ 1024, R 8
 
 
-@pytest.mark.parametrize("variant", ["fixed", "dual", "fused", "fusedp", "one"])
+@pytest.mark.parametrize("variant", ["fixed", "dual", "fused", "fusedp", "fold", "one"])
 def test_fft_kernel_variants_parity(S, monkeypatch, variant):
     # SPEC_FFT_VARIANT pins the kernel variant the autotuner would otherwise
     # choose by timing; every variant must meet the same bar
@@ -345,14 +345,15 @@ def test_fft_kernel_variants_parity(S, monkeypatch, variant):
             err = rel_rows(got, O.fft_padded(x, n_fft))
             assert err.max() <= TOL, (variant, batch, n, n_fft, err.max())
         # rows at an odd stride (unaligned starts) into a wider output
-        x = traces(3, 1024, 11)
-        base = torch.zeros((3, 1031), dtype=torch.float32, device="cuda")
-        base[:, :1024] = dev(x)
-        out = torch.full((3, 4200), float("nan"), dtype=torch.complex64, device="cuda")
-        S.spec_fft(c, base, 20e12, 8192, n=1024, out=out)
-        got = out[:, :4097].cpu().numpy()
-        assert rel_rows(got, O.fft_padded(x, 8192)).max() <= TOL
-        assert torch.isnan(out[:, 4097:].real).all()
+        for n in (1024, 2048):
+            x = traces(3, n, 11 + n)
+            base = torch.zeros((3, n + 7), dtype=torch.float32, device="cuda")
+            base[:, :n] = dev(x)
+            out = torch.full((3, 4200), float("nan"), dtype=torch.complex64, device="cuda")
+            S.spec_fft(c, base, 20e12, 8192, n=n, out=out)
+            got = out[:, :4097].cpu().numpy()
+            assert rel_rows(got, O.fft_padded(x, 8192)).max() <= TOL, (variant, n)
+            assert torch.isnan(out[:, 4097:].real).all()
 
 
 @pytest.mark.parametrize("lanes", ["1", "2"])
