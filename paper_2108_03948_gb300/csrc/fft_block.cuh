@@ -276,6 +276,27 @@ template <bool INV, class V> __device__ __forceinline__ void dft16(V* a) {
     t = a[11]; a[11] = a[14]; a[14] = t;
 }
 
+// The same DFT when only a[0 .. 3] can be nonzero (a[4 .. 15] are ignored):
+// each first-stage 4-point DFT sees one input, so it is a copy.
+template <bool INV, class V> __device__ __forceinline__ void dft16_lo4(V* a) {
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) a[4 * k1 + n2] = a[n2];
+    a[5] = tw16<1, INV>(a[5]);  a[6] = tw16<2, INV>(a[6]);   a[7] = tw16<3, INV>(a[7]);
+    a[9] = tw16<2, INV>(a[9]);  a[10] = tw16<4, INV>(a[10]); a[11] = tw16<6, INV>(a[11]);
+    a[13] = tw16<3, INV>(a[13]); a[14] = tw16<6, INV>(a[14]); a[15] = tw16<9, INV>(a[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    V t;
+    t = a[1]; a[1] = a[4]; a[4] = t;
+    t = a[2]; a[2] = a[8]; a[8] = t;
+    t = a[3]; a[3] = a[12]; a[12] = t;
+    t = a[6]; a[6] = a[9]; a[9] = t;
+    t = a[7]; a[7] = a[13]; a[13] = t;
+    t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
 // cos(pi k/16), k = 0 .. 8
 __host__ __device__ constexpr float cos_pi16(int k) {
     return k == 0 ? 1.0f : k == 1 ? 0.98078528040323044913f : k == 2 ? 0.92387953251128675613f
@@ -481,6 +502,15 @@ template <int LF, bool INV, class V = float2, int EMAX = 16, class TWT = typenam
 
     static __device__ __forceinline__ void run(V (&v)[E], SM* s, int t, const TW* tw) {
         passes<0>(v, s, t, tw);
+    }
+
+    // The whole FFT when only v[0 .. 3] of every thread can be nonzero (the
+    // input is zero from position 4 T on): the first radix-16 pass needs no
+    // twiddles and its first stage reduces to copies.
+    static __device__ __forceinline__ void run_lo4(V (&v)[E], SM* s, int t, const TW* tw) {
+        static_assert(E == 16 && S::radix(0) == 16, "radix-16 first pass");
+        dft16_lo4<INV>(v);
+        passes<1>(v, s, t, tw);
     }
 
     // Passes 0 .. NP-1 only (compute and the exchanges between them): the

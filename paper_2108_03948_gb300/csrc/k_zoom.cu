@@ -87,7 +87,10 @@ __device__ __forceinline__ void zoom_fir_blocked(const float4* tap, const float*
     }
 }
 
-template <int K>
+// LO4: the launch guarantees L_out <= 4 T, so only the first four FFT inputs
+// of a thread can be nonzero (BlockFFT::run_lo4); a separate instance, since
+// both FFT forms in one kernel spill at 64 registers.
+template <int K, bool LO4 = false>
 __global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 1024 ? 1 : (FFTShape<K>::T >= 32 ? 1024 / FFTShape<K>::T : 32)) k_zoom(ZoomArgs a) {
     using FFT = BlockFFT<K, false>;
     constexpr int E = FFT::E, T = FFT::T;
@@ -130,7 +133,23 @@ __global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 1024 ? 1 : (
     // extended trace xe[j] = x[j - J] (zero outside [0, N)), by phase
     const float* xr = a.x + xo;
     const int total = D * rs;
-    if (logd >= 0) {
+    if (logd >= 2 && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(xr) & 15) == 0) {
+        // 16-byte loads of four samples; the zeros before and after the trace
+        // separately (j + 4 q: the warp's stores of one sample index fall in
+        // one phase row at most two rows, consecutive columns)
+        const int dm = D - 1;
+        for (int j = t; j < J; j += T) xs[(j & dm) * rs + (j >> logd)] = 0.f;
+        for (int j = J + n + t; j < total; j += T) xs[(j & dm) * rs + (j >> logd)] = 0.f;
+        const float4* x4 = reinterpret_cast<const float4*>(xr);
+        for (int q = t; q < (n >> 2); q += T) {
+            const float4 x = __ldg(x4 + q);
+            const int j = 4 * q + J;
+            xs[(j & dm) * rs + (j >> logd)] = x.x;
+            xs[((j + 1) & dm) * rs + ((j + 1) >> logd)] = x.y;
+            xs[((j + 2) & dm) * rs + ((j + 2) >> logd)] = x.z;
+            xs[((j + 3) & dm) * rs + ((j + 3) >> logd)] = x.w;
+        }
+    } else if (logd >= 0) {
         const int dm = D - 1;
         for (int j = t; j < total; j += T) {
             const int src = j - J;
@@ -149,12 +168,21 @@ __global__ void __launch_bounds__(FFTShape<K>::T, FFTShape<K>::T >= 1024 ? 1 : (
     zoom_fir_blocked<3, T>(tap, xs, s, n_taps, lout, rs, Cn, D, t);
     __syncthreads();
     float2 v[E];
+    if constexpr (LO4) {
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-        const int m = t + T * i;
-        v[i] = m < lout ? s[pidx(m)] : make_float2(0.f, 0.f);
+        for (int i = 0; i < 4; ++i) {
+            const int m = t + T * i;
+            v[i] = m < lout ? s[pidx(m)] : make_float2(0.f, 0.f);
+        }
+        FFT::run_lo4(v, s, t, a.tw);
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int m = t + T * i;
+            v[i] = m < lout ? s[pidx(m)] : make_float2(0.f, 0.f);
+        }
+        FFT::run(v, s, t, a.tw);
     }
-    FFT::run(v, s, t, a.tw);
     float2* Xr = a.X + Xo;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -410,7 +438,16 @@ static ZoomKernel zoom_kernel2_for(int K) {
     }
 }
 
-static ZoomKernel zoom_kernel_for(int K) {
+static ZoomKernel zoom_kernel_for(int K, bool lo4 = false) {
+    if (lo4) {
+        switch (K) {
+            case 1024: return k_zoom<1024, true>;
+            case 2048: return k_zoom<2048, true>;
+            case 4096: return k_zoom<4096, true>;
+            case 8192: return k_zoom<8192, true>;
+            default: break;
+        }
+    }
     switch (K) {
         case 1: return k_zoom<1>;
         case 2: return k_zoom<2>;
@@ -471,7 +508,8 @@ cudaError_t zoom_launch(const ZoomPlan& p, const float* x, int64_t batch, int64_
                         int lanes) {
     if (batch == 0) return cudaSuccess;
     const bool dual = p.dual && batch >= 2 && lanes != 1;
-    ZoomKernel k = dual ? zoom_kernel2_for(p.K) : zoom_kernel_for(p.K);
+    // L_out <= 4 T (T = K/16): the FFT's first pass sees four inputs per thread
+    ZoomKernel k = dual ? zoom_kernel2_for(p.K) : zoom_kernel_for(p.K, (int64_t)p.lout * 4 <= p.K);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = dual ? p.smem2 : p.smem;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
