@@ -441,10 +441,12 @@ static ZoomKernel zoom_kernel2_for(int K) {
 static ZoomKernel zoom_kernel_for(int K, bool lo4 = false) {
     if (lo4) {
         switch (K) {
+            case 512: return k_zoom<512, true>;
             case 1024: return k_zoom<1024, true>;
             case 2048: return k_zoom<2048, true>;
             case 4096: return k_zoom<4096, true>;
             case 8192: return k_zoom<8192, true>;
+            case 16384: return k_zoom<16384, true>;
             default: break;
         }
     }
@@ -558,9 +560,9 @@ size_t fir_smem_for(int n_taps, int d) { return (size_t)n_taps * 16 + (size_t)d 
 int fir_chunk() { return kFirChunk; }
 
 cudaError_t zoom_ragged_launch(int K, const RaggedItem* items, int64_t count, size_t smem, const float* x_pool,
-                               const float* taps_pool, const float2* tw, float2* X_pool, cudaStream_t st) {
+                               const float* taps_pool, const float2* tw, float2* X_pool, cudaStream_t st, bool lo4) {
     if (count == 0) return cudaSuccess;
-    ZoomKernel k = zoom_kernel_for(K);
+    ZoomKernel k = zoom_kernel_for(K, lo4);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -45,6 +45,7 @@ struct RaggedClass {
     int lanes = 1;
     bool in_queue = false;   // the work queue covers these traces too
     size_t smem = 0;     // Zoom one-CTA: the largest need in the class
+    bool lo4 = false;    // Zoom one-CTA: every trace has L_out <= K/4 (sparse first FFT pass)
     int64_t first = 0, count = 0;
     const float2* tab = nullptr;
     float tuned_us = 0.f;
@@ -120,7 +121,7 @@ cudaError_t launch_class(spec_ctx* c, RaggedPlan* P, const RaggedClass& k, cudaS
         case 1:
             return czt_ragged_launch(k.L, it, k.count, x, P->tables, tw_for(c, k.L), X, s);
         case 2:
-            return zoom_ragged_launch(k.K, it, k.count, k.smem, x, taps, tw_for(c, k.K), X, s);
+            return zoom_ragged_launch(k.K, it, k.count, k.smem, x, taps, tw_for(c, k.K), X, s, k.lo4);
         default:
             return c2c_launch(k.fp, P->work, 0, 0, k.count, k.K / 2, tw_for(c, k.fp.LZ), k.tab, X, 0, s, it);
     }
@@ -434,6 +435,8 @@ spec_status build_plan(spec_ctx* c, int kind, const spec_desc* d, int64_t count,
         } else if (path == 2) {
             k.K = std::get<1>(kv.first);
             k.smem = gsmem[kv.first];
+            k.lo4 = true;
+            for (const Tmp& t : kv.second) k.lo4 = k.lo4 && (int64_t)t.it.lout * 4 <= k.K;
         } else {
             k.K = std::get<1>(kv.first);
             std::string why;

@@ -280,8 +280,10 @@ size_t zoom_smem_for(int n_taps, int d, int rs, int K);
 int fir_rows(int64_t n_taps, int64_t d);
 size_t fir_smem_for(int n_taps, int d);
 int fir_chunk();
+// lo4: every trace of the class has L_out <= K/4 (the kernel's sparse first FFT pass)
 cudaError_t zoom_ragged_launch(int K, const RaggedItem* items, int64_t count, size_t smem, const float* x_pool,
-                               const float* taps_pool, const float2* tw, float2* X_pool, cudaStream_t st);
+                               const float* taps_pool, const float2* tw, float2* X_pool, cudaStream_t st,
+                               bool lo4 = false);
 cudaError_t zoom_fir_ragged_launch(const RaggedItem* items, int64_t count, int chunks_max, size_t smem,
                                    const float* x_pool, const float* taps_pool, float2* work, cudaStream_t st);
 

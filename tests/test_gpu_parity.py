@@ -142,8 +142,9 @@ ZOOM_CASES = [
     (3, 8192, 0.5e12, 1.5e12, 16, 127, 65536), (2, 8192, 0.5e12, 1.5e12, 4, 31, 65536),
     (4, 30, 0.5e12, 1.5e12, 2, 5, 64), (3, 1000, 0.1e12, 2.0e12, 8, 45, 8192), (2, 2047, 3e12, 4e12, 2, 64, 16384),
     (1, 2048, 0.2e12, 2.5e12, 4, 63, 16384), (5, 3000, 0.2e12, 0.9e12, 3, 40, 24576),
-    # L_out above K/4 with 16-byte staging loads (D = 4): the FFT's full first pass
-    (3, 4096, 0.5e12, 1.5e12, 4, 63, 8192),
+    # L_out above K/4 with 16-byte staging loads (D = 4): the FFT's full first pass;
+    # K = 512 with L_out <= K/4 (sparse first pass, one warp per trace)
+    (3, 4096, 0.5e12, 1.5e12, 4, 63, 8192), (3, 400, 0.5e12, 1.5e12, 4, 31, 2048),
     # FIR kernel + pruned cluster FFT: K = 32768 (4-CTA cluster), a 100 k-sample trace,
     # the long-trace shape (262144 samples, D = 64, 255 taps, K = 32768), D not a power of two
     (3, 8000, 0.5e12, 2.5e12, 2, 101, 65536), (2, 100000, 0.3e12, 0.4e12, 64, 255, 262144),
