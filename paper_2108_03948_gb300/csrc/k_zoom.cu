@@ -52,6 +52,7 @@ template <int B, int T>
 __device__ __forceinline__ void zoom_fir_blocked(const float4* tap, const float* xs, float2* s, int n_taps,
                                                  int lout, int rs, uint64_t Cn, int D, int t) {
     const int J = n_taps - 1;
+    const float2 step = unit_fixed(Cn * (uint64_t)D, true);     // e^{-j w D}
     for (int m0 = B * t; m0 < lout; m0 += B * T) {
         float re[B], im[B];
 #pragma unroll
@@ -76,13 +77,14 @@ __device__ __forceinline__ void zoom_fir_blocked(const float4* tap, const float*
                 }
             }
         }
+        // e^{-j w m D} for m = m0 .. m0 + B - 1: the first from the exact
+        // phase, the next by the one-output step (B - 1 products)
+        float2 rot = unit_fixed(Cn * ((uint64_t)m0 * (uint64_t)D), true);
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int m = m0 + u;
-            if (m < lout) {
-                const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
-                s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
-            }
+            if (m < lout) s[pidx(m)] = cmul(make_float2(re[u], im[u]), rot);
+            if (u + 1 < B) rot = cmul(rot, step);
         }
     }
 }
@@ -199,6 +201,7 @@ template <int B, int T>
 __device__ __forceinline__ void zoom_fir_blocked2(const float4* tap, const float2* xs, float4* s, int n_taps,
                                                   int lout, int rs, uint64_t Cn, int D, int t) {
     const int J = n_taps - 1;
+    const float2 step = unit_fixed(Cn * (uint64_t)D, true);     // e^{-j w D}
     for (int m0 = B * t; m0 < lout; m0 += B * T) {
         float2 re[B], im[B];
 #pragma unroll
@@ -224,13 +227,12 @@ __device__ __forceinline__ void zoom_fir_blocked2(const float4* tap, const float
                 }
             }
         }
+        float2 rot = unit_fixed(Cn * ((uint64_t)m0 * (uint64_t)D), true);
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int m = m0 + u;
-            if (m < lout) {
-                const float2 rot = unit_fixed(Cn * ((uint64_t)m * (uint64_t)D), true);
-                sts(s, pidx(m), mul_tw<false>(C2{re[u], im[u]}, rot));
-            }
+            if (m < lout) sts(s, pidx(m), mul_tw<false>(C2{re[u], im[u]}, rot));
+            if (u + 1 < B) rot = cmul(rot, step);
         }
     }
 }
